@@ -1,0 +1,209 @@
+/* sra.h — sound range analysis of MLP implicit functions on GB300 (sm_103a).
+ *
+ * C ABI of the library libsra.so. It bounds a scalar MLP f: R^3 -> R over
+ * many boxes and ray segments with affine (or interval) arithmetic and uses
+ * the bounds to classify octree nodes and to cast rays. Method: Sharp &
+ * Jacobson, "Spelunking the Deep: Guaranteed Queries on General Neural
+ * Implicit Surfaces via Range Analysis", SIGGRAPH 2022 (arXiv 2202.02444).
+ *
+ * Conventions for every entry point:
+ *   - Array arguments marked "device" are caller-owned device pointers
+ *     (e.g. torch tensors' data_ptr()); "host" marks host pointers. The
+ *     library owns only the network copy made by sra_load_mlp and transient
+ *     scratch it allocates stream-ordered (cudaMallocAsync) on the call's
+ *     stream.
+ *   - Calls enqueue work on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and return without synchronising unless stated. Launch and
+ *     argument errors are returned at once; nothing aborts the process.
+ *   - On an error the function returns a non-zero sra_status and
+ *     sra_last_error() describes it (thread-local string).
+ *   - Calls on distinct streams may run concurrently on one network.
+ */
+#ifndef SRA_H
+#define SRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sra_net sra_net; /* opaque; owns device copies of the weights */
+
+typedef enum {
+    SRA_OK = 0,
+    SRA_EINVAL = 1,        /* bad argument (null pointer, size, option) */
+    SRA_ENOMEM = 2,        /* device or host allocation failed */
+    SRA_ECUDA = 3,         /* a CUDA call failed; see sra_last_error() */
+    SRA_ETIMEOUT = 4,      /* a bounded device wait ran out */
+    SRA_ECAPACITY = 5,     /* an output buffer was too small; needed size reported */
+    SRA_EUNSUPPORTED = 6   /* network shape / option not supported by a kernel */
+} sra_status;
+
+/* uint8 box classes (Proc. 1 "RangeBound"). */
+enum { SRA_UNKNOWN = 0, SRA_POSITIVE = 1, SRA_NEGATIVE = 2 };
+
+/* Activations (App. A Table "affine_nonlinearities"). */
+enum { SRA_ACT_IDENTITY = 0, SRA_ACT_RELU = 1, SRA_ACT_ELU = 2, SRA_ACT_SIN = 3 };
+
+/* Range arithmetic (Sec. 3.1 interval; Sec. 3.3 affine condensation policies). */
+enum {
+    SRA_ARITH_INTERVAL = 0,
+    SRA_ARITH_AFFINE_FIXED = 1,    /* keep only the input-domain symbols */
+    SRA_ARITH_AFFINE_TRUNCATE = 2, /* keep the K largest symbols (column L1 norm) */
+    SRA_ARITH_AFFINE_FULL = 3      /* keep every symbol (small networks only) */
+};
+
+/* Slope of the activation linearisation: Chebyshev (App. A) or min-range. */
+enum { SRA_SLOPE_CHEBYSHEV = 0, SRA_SLOPE_MINRANGE = 1 };
+
+/* Arithmetic the bound is computed in.
+ *   FP32:       plain single precision, no rounding control (the paper's form,
+ *               which Sec. 3.4 states needs none in practice).
+ *   FP64:       plain double precision.
+ *   BF16_SOUND: noise-symbol products on BF16 tensor cores with FP32
+ *               accumulation, center and x_inf in FP32, and an a-priori
+ *               rounding radius folded into x_inf so the bound stays
+ *               guaranteed (outward-rounded range). */
+enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2 };
+
+/* Tree refinement: 8-way octree (one level = 3 k-d levels on a cube) or the
+ * widest-axis binary split of Proc. 3 ("BuildSpatialTree"). */
+enum { SRA_SPLIT_OCTREE = 0, SRA_SPLIT_KD = 1 };
+
+/* Network description (host memory, read during sra_load_mlp only).
+ * widths[0] is the first linear layer's input width: 3, or 3 + 6*pe_octaves
+ * when the input x in R^3 is encoded as [x, then per octave k:
+ * sin(2^k pi x_0..2), cos(2^k pi x_0..2)]. widths[n_layers] must be 1.
+ * acts[l] (l < n_layers-1) follows linear layer l; the last layer is linear.
+ * params packs, for each layer l, the row-major W_l (widths[l+1] x widths[l])
+ * followed by b_l (widths[l+1]), as float32. */
+typedef struct {
+    int32_t n_layers;
+    const int32_t *widths;
+    const int32_t *acts;
+    const float *params;
+    int32_t pe_octaves;
+} sra_mlp_desc;
+
+/* Query options; sra_default_opts() fills the paper's defaults. */
+typedef struct {
+    int32_t arith;       /* SRA_ARITH_* */
+    int32_t K;           /* kept noise symbols for affine-truncate (excl. x_inf) */
+    int32_t slope;       /* SRA_SLOPE_* */
+    int32_t precision;   /* SRA_PREC_* */
+    int32_t recheck;     /* 1: re-bound in FP64 every box whose lo or hi lies
+                            within the band of zero, and keep the FP64 result */
+    float recheck_band;  /* band half-width relative to |center| + radius */
+    int32_t split;       /* SRA_SPLIT_* */
+    float delta;         /* convergence tolerance (Sec. 4.1), > 0 */
+    float t_max;         /* ray miss distance (Sec. 4.2) */
+    float sigma0;        /* initial ray step (Sec. 4.2: t_max / 10) */
+    float eta_plus;      /* step growth on success (1.5) */
+    float eta_minus;     /* step shrink on failure (0.5) */
+    float safety;        /* step fraction taken (App. B: 0.98) */
+    int64_t max_iters;   /* per-ray iteration cap; the ray then reports NaN */
+} sra_opts;
+
+/* Octree / k-d node: integer cell coordinates at `level` inside the root box
+ * given with each call. Octree: 2^level cells per axis. k-d: the per-axis
+ * number of halvings follows the widest-axis rule of Proc. 3 from the root
+ * extents (lowest axis on ties). */
+typedef struct {
+    uint16_t ix, iy, iz, level;
+} sra_node;
+
+/* Indices into the int64 counts array of sra_classify_and_split. */
+enum {
+    SRA_CNT_CHILDREN = 0, /* children appended to frontier_out (total, may exceed cap) */
+    SRA_CNT_LEAVES = 1,   /* UNKNOWN leaves at max_level appended (may exceed cap) */
+    SRA_CNT_POSITIVE = 2, /* nodes classified POSITIVE */
+    SRA_CNT_NEGATIVE = 3, /* nodes classified NEGATIVE */
+    SRA_CNT_UNKNOWN = 4,  /* nodes classified UNKNOWN */
+    SRA_CNT_RECHECKED = 5,/* nodes re-bounded in FP64 */
+    SRA_CNT_N = 8
+};
+
+/* Fill *o with the defaults: affine-fixed, Chebyshev, FP32, no re-check,
+ * band 1e-5, octree, delta 1e-3, t_max 10, sigma0 1, eta 1.5 / 0.5,
+ * safety 0.98, max_iters 1<<20 (Sec. 4.1, Sec. 4.2, App. B). */
+void sra_default_opts(sra_opts *o);
+
+/* Copy a network to the current device (App. A: the MLP f whose affine
+ * propagation all queries use). Host `desc` may be freed after the call.
+ * Errors: SRA_EINVAL (shape), SRA_EUNSUPPORTED (more than 24 layers or a
+ * width above 512), SRA_ENOMEM, SRA_ECUDA. Synchronous. */
+sra_status sra_load_mlp(const sra_mlp_desc *desc, sra_net **out);
+
+/* Free a network (synchronises the device first). NULL is accepted. */
+sra_status sra_free_mlp(sra_net *net);
+
+/* Proc. 1 (RangeBound) on n axis-aligned boxes: box i is
+ * centers[i] +- halfw[i] (device float[n][3] each). Writes the output range
+ * lo[i], hi[i] (device float[n]) and the class cls[i] (device uint8[n]):
+ * POSITIVE iff lo > 0, NEGATIVE iff hi < 0, else UNKNOWN. lo/hi may be NULL.
+ * With opts->recheck the boxes whose lo or hi lies within the band of zero
+ * are re-bounded in FP64 on the GPU and their lo/hi/cls replaced.
+ * n == 0 is a no-op.
+ * Errors: SRA_EINVAL, SRA_EUNSUPPORTED (K / width beyond the kernels' limits),
+ * SRA_ECUDA. Asynchronous on `stream`. */
+sra_status sra_bound_boxes(const sra_net *net, const sra_opts *opts, const float *centers,
+                           const float *halfw, int64_t n, float *lo, float *hi,
+                           uint8_t *cls, void *stream);
+
+/* One batched round of Proc. 3 (Sec. 4.5 builds the tree level by level in batches)
+ * at a fixed depth (Sec. 4.7). For each node of frontier_in (device
+ * sra_node[n_in]) inside the root box [root_lo, root_hi] (host float[3]):
+ * bound it; if UNKNOWN and level < max_level append its children (8 for the
+ * octree, 2 for k-d) to frontier_out; if UNKNOWN and level == max_level
+ * append it to leaves_out. Output positions start at the values already in
+ * counts[SRA_CNT_CHILDREN] / counts[SRA_CNT_LEAVES] (device int64[8]; zero
+ * it before the first call of a level, so chunked calls append) and follow
+ * the input order (deterministic). Records beyond cap_out / cap_leaves are
+ * not written but still counted, so a caller detects overflow after the
+ * stream syncs by counts[...] > cap. counts[2..5] accumulate per-class and
+ * re-check tallies. Uses stream-ordered scratch of about n_in * 9 bytes.
+ * Errors: SRA_EINVAL, SRA_EUNSUPPORTED, SRA_ENOMEM, SRA_ECUDA. Asynchronous. */
+sra_status sra_classify_and_split(const sra_net *net, const sra_opts *opts,
+                                  const float *root_lo, const float *root_hi,
+                                  const sra_node *frontier_in, int64_t n_in, int32_t max_level,
+                                  sra_node *frontier_out, int64_t cap_out,
+                                  sra_node *leaves_out, int64_t cap_leaves,
+                                  int64_t *counts, void *stream);
+
+/* Proc. 2 (CastRay) for n rays p = origins[i], r = dirs[i] (device
+ * float[n][3]; r need not be unit length; t is in units of r). Writes
+ * t_hit[i] (device float[n]): the returned t on a hit, +inf for NO_HIT, NaN
+ * when opts->max_iters ran out; and iters[i] (device int32[n], may be NULL):
+ * loop iterations taken. One persistent launch refills finished ray slots.
+ * Errors: SRA_EINVAL (delta <= 0, bad steps), SRA_EUNSUPPORTED, SRA_ECUDA.
+ * Asynchronous. */
+sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *origins,
+                         const float *dirs, int64_t n, float *t_hit, int32_t *iters,
+                         void *stream);
+
+/* Proc. 3 to a fixed depth from the root box [xl, xu] (host float[3]): runs
+ * sra_classify_and_split level by level and writes the UNKNOWN nodes at
+ * `depth` to leaves_out (device sra_node[cap]) in level-order; these are the
+ * cells that hierarchical mesh extraction (Sec. 4.7) visits. *n_leaves
+ * (host) receives the leaf count. Per-level POSITIVE/NEGATIVE/UNKNOWN counts
+ * are written to level_counts (host int64[(depth+1)*3], may be NULL).
+ * Synchronises the stream once per level. Errors: SRA_ECAPACITY when the
+ * leaves exceed cap (*n_leaves holds the needed count, the first cap are
+ * written), SRA_EINVAL, SRA_EUNSUPPORTED, SRA_ENOMEM, SRA_ECUDA. */
+sra_status sra_extract_leaves(const sra_net *net, const sra_opts *opts, const float *xl,
+                              const float *xu, int32_t depth, sra_node *leaves_out,
+                              int64_t cap, int64_t *n_leaves, int64_t *level_counts,
+                              void *stream);
+
+/* Plain forward evaluation f(x) for n points (device float[n][3] -> device
+ * float[n]) in the network's FP32 weights. Asynchronous. */
+sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, void *stream);
+
+/* Description of the last error on this thread ("" if none). */
+const char *sra_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SRA_H */

@@ -81,13 +81,13 @@ def lib():
         L.orc_range_bound.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
                                       dp, dp, dp, dp]
         L.orc_bound_boxes.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), C.c_int64, dp, dp,
-                                      dp, dp, dp, dp, C.POINTER(C.c_int32), C.c_int]
+                                      dp, dp, dp, dp, C.POINTER(C.c_int32), dp, C.c_int]
         L.orc_build_tree.restype = C.c_int64
         L.orc_build_tree.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
                                      C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
         L.orc_classify_nodes.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
                                          C.c_int64, C.c_void_p, C.POINTER(C.c_int32), dp, dp,
-                                         C.c_int]
+                                         dp, C.c_int]
         L.orc_cast_ray.restype = C.c_int
         L.orc_cast_rays.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), C.POINTER(_RayOpts),
                                     C.c_int64, dp, dp, dp, C.POINTER(C.c_int64),
@@ -169,12 +169,12 @@ def bound_boxes(net, centers, halfw, arith="fixed", K=0, slope="chebyshev", nthr
     c = np.ascontiguousarray(np.asarray(centers, np.float64).reshape(-1, 3))
     h = np.ascontiguousarray(np.asarray(halfw, np.float64).reshape(-1, 3))
     m = len(c)
-    lo, hi, y0, rad = (np.empty(m) for _ in range(4))
+    lo, hi, y0, rad, gap = (np.empty(m) for _ in range(5))
     cls = np.empty(m, np.int32)
     lib().orc_bound_boxes(C.byref(n.s), C.byref(o), m, _dp(c), _dp(h), _dp(lo), _dp(hi),
                           _dp(y0), _dp(rad), cls.ctypes.data_as(C.POINTER(C.c_int32)),
-                          int(nthreads))
-    return {"lo": lo, "hi": hi, "y0": y0, "rad": rad, "cls": cls}
+                          _dp(gap), int(nthreads))
+    return {"lo": lo, "hi": hi, "y0": y0, "rad": rad, "cls": cls, "sel_gap": gap}
 
 
 def build_tree(net, xl, xu, max_level, split=OCTREE, arith="fixed", K=0,
@@ -206,11 +206,12 @@ def classify_nodes(net, nodes, xl, xu, split=OCTREE, arith="fixed", K=0,
     cls = np.empty(len(nodes), np.int32)
     lo = np.empty(len(nodes))
     hi = np.empty(len(nodes))
+    gap = np.empty(len(nodes))
     lib().orc_classify_nodes(C.byref(n.s), C.byref(o), _dp(xl), _dp(xu), int(split),
                              len(nodes), nd.ctypes.data,
                              cls.ctypes.data_as(C.POINTER(C.c_int32)), _dp(lo), _dp(hi),
-                             int(nthreads))
-    return cls, lo, hi
+                             _dp(gap), int(nthreads))
+    return cls, lo, hi, gap
 
 
 def cast_rays(net, origins, dirs, arith="fixed", K=0, slope="chebyshev", delta=1e-3,

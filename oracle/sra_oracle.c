@@ -74,7 +74,7 @@ static double act_eval(int act, double x) {
     }
 }
 
-/* Range of cos on [l,u] ("computed via modular arithmetic", App. A). */
+/* Range of cos on [l,u], located through multiples of 2 pi (App. A). */
 static void cos_range(double l, double u, double *lo, double *hi) {
     if (u - l >= TWO_PI) { *lo = -1.0; *hi = 1.0; return; }
     double cl = cos(l), cu = cos(u);
@@ -233,6 +233,11 @@ typedef struct {
     int idx;
 } cand_t;
 
+/* Test diagnostic: smallest relative gap between the last kept and the first
+ * dropped truncate score seen since the last reset (per thread). A GPU that
+ * sums scores in another order may keep the other column when this is tiny. */
+static _Thread_local double t_sel_gap = INFINITY;
+
 static int cand_cmp(const void *pa, const void *pb) {
     const cand_t *a = (const cand_t *)pa, *b = (const cand_t *)pb;
     if (a->score > b->score) return -1;
@@ -291,6 +296,12 @@ static aform af_nonlinear(aform *f, const double *alpha, const double *beta,
         qsort(cs, (size_t)ncand, sizeof(cand_t), cand_cmp);
         int nk = o->K < ncand ? o->K : ncand;
         for (int q = 0; q < nk; ++q) keep[cs[q].idx] = 1;
+        if (nk > 0 && nk < ncand) {
+            /* equal zero scores are exact on any machine: no ambiguity */
+            double top = cs[nk - 1].score;
+            double g = (top > 0.0) ? (top - cs[nk].score) / top : INFINITY;
+            if (g < t_sel_gap) t_sel_gap = g;
+        }
         free(cs);
     }
     int nkeep = 0;
@@ -528,14 +539,16 @@ int orc_range_bound(const orc_net *net, const orc_opts *o, const double *c,
 void orc_bound_boxes(const orc_net *net, const orc_opts *o, int64_t n,
                      const double *centers, const double *halfw, double *lo,
                      double *hi, double *y0, double *rad, int32_t *cls,
-                     int nthreads) {
+                     double *sel_gap, int nthreads) {
     if (nthreads <= 0) nthreads = orc_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
     for (int64_t i = 0; i < n; ++i) {
         double axes[9] = {0};
         for (int d = 0; d < 3; ++d) axes[d * 3 + d] = halfw[3 * i + d];
         double l, h, c0, r;
+        t_sel_gap = INFINITY;
         int k = orc_range_bound(net, o, centers + 3 * i, axes, 3, &l, &h, &c0, &r);
+        if (sel_gap) sel_gap[i] = t_sel_gap;
         if (lo) lo[i] = l;
         if (hi) hi[i] = h;
         if (y0) y0[i] = c0;
@@ -649,7 +662,7 @@ int64_t orc_build_tree(const orc_net *net, const orc_opts *o, const double *xl,
 void orc_classify_nodes(const orc_net *net, const orc_opts *o, const double *xl,
                         const double *xu, int split, int64_t n,
                         const orc_node *nodes, int32_t *cls, double *lo,
-                        double *hi, int nthreads) {
+                        double *hi, double *sel_gap, int nthreads) {
     if (nthreads <= 0) nthreads = orc_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
     for (int64_t i = 0; i < n; ++i) {
@@ -660,7 +673,9 @@ void orc_classify_nodes(const orc_net *net, const orc_opts *o, const double *xl,
             axes[d * 3 + d] = bh[d] - c[d];
         }
         double l, h, y0, r;
+        t_sel_gap = INFINITY;
         int k = orc_range_bound(net, o, c, axes, 3, &l, &h, &y0, &r);
+        if (sel_gap) sel_gap[i] = t_sel_gap;
         if (cls) cls[i] = k;
         if (lo) lo[i] = l;
         if (hi) hi[i] = h;

@@ -66,11 +66,13 @@ int orc_range_bound(const orc_net *net, const orc_opts *o, const double *c,
                     const double *axes, int s, double *lo, double *hi,
                     double *y0, double *rad);
 
-/* Batch of axis-aligned boxes (center, half-width per axis). */
+/* Batch of axis-aligned boxes (center, half-width per axis). sel_gap (may be
+ * NULL) receives, per box, the smallest relative gap between the last kept
+ * and the first dropped affine-truncate column score (+inf if none). */
 void orc_bound_boxes(const orc_net *net, const orc_opts *o, int64_t n,
                      const double *centers, const double *halfw, double *lo,
                      double *hi, double *y0, double *rad, int32_t *cls,
-                     int nthreads);
+                     double *sel_gap, int nthreads);
 
 /* Proc. 3 (BuildSpatialTree) stopped at a fixed depth, over the root box
  * [xl,xu]. split = ORC_SPLIT_OCTREE classifies cubes and splits all three
@@ -88,7 +90,7 @@ int64_t orc_build_tree(const orc_net *net, const orc_opts *o, const double *xl,
 void orc_classify_nodes(const orc_net *net, const orc_opts *o, const double *xl,
                         const double *xu, int split, int64_t n,
                         const orc_node *nodes, int32_t *cls, double *lo,
-                        double *hi, int nthreads);
+                        double *hi, double *sel_gap, int nthreads);
 
 typedef struct {
     double delta, t_max, sigma0, eta_plus, eta_minus, safety;

@@ -1,0 +1,621 @@
+// C-ABI layer of libsra.so: argument validation, kernel-variant choice,
+// shared-memory layout, stream-ordered scratch and the level loop of the
+// fixed-depth tree build (Proc. 3). Every step of the path runs in the
+// kernels of this library.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+
+using namespace sra;
+
+struct sra_net {
+    NetDev dev;
+    int L = 0, pe = 0, din = 0;
+    std::vector<int> widths, acts;
+    int rows = 0;      // max width (state matrix rows)
+    int H = 0;         // threads per box
+    int new_syms = 0;  // symbols created by all nonlinearities (affine-full sizing)
+    void *buf = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sra_status fail(sra_status s, const char *fmt, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
+    g_err = b;
+    return s;
+}
+
+#define SRA_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(SRA_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kMaxSmem = 232448;  // 227 KB opt-in per CTA on sm_100-class GPUs
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Smallest instantiated KMAX >= need, or 0.
+int pick_kmax(int need) {
+    for (int k : kKmaxList)
+        if (k >= need) return k;
+    return 0;
+}
+
+sra_status kmax_for(const sra_net *n, const sra_opts *o, int s, int *kmax) {
+    int need = 1;
+    switch (o->arith) {
+    case SRA_ARITH_INTERVAL: need = 1; break;
+    case SRA_ARITH_AFFINE_FIXED: need = s; break;
+    case SRA_ARITH_AFFINE_TRUNCATE:
+        if (o->K < 1) return fail(SRA_EINVAL, "affine-truncate needs K >= 1 (got %d)", o->K);
+        need = o->K > s ? o->K : s;
+        break;
+    case SRA_ARITH_AFFINE_FULL: need = s + n->new_syms; break;
+    default: return fail(SRA_EINVAL, "unknown arith %d", o->arith);
+    }
+    *kmax = pick_kmax(need);
+    if (!*kmax) return fail(SRA_EUNSUPPORTED, "needs %d noise columns; the kernels hold at most 128", need);
+    return SRA_OK;
+}
+
+// Per-box shared-memory layout and boxes per CTA.
+sra_status make_cfg(const sra_net *n, const sra_opts *o, int kmax, int tsize, int target_threads,
+                    RangeCfg *cfg) {
+    memset(cfg, 0, sizeof *cfg);
+    cfg->arith = o->arith;
+    cfg->K = o->K;
+    cfg->slope = o->slope;
+    cfg->H = n->H;
+    cfg->rows = n->rows;
+    const int RS = engine_row_stride(kmax);
+    size_t off = 0;
+    cfg->x_off = (int)off;
+    off = align16(off + (size_t)n->rows * RS * tsize);
+    cfg->score_off = (int)off;
+    off = align16(off + (size_t)(kmax + n->rows) * tsize);
+    cfg->part_off = (int)off;
+    off = align16(off + (size_t)(n->H / 32) * (kmax + 4) * tsize);
+    cfg->outv_off = (int)off;
+    off = align16(off + (size_t)(kmax + 4) * tsize);
+    cfg->keep_off = (int)off;
+    off = align16(off + (size_t)(kmax + n->rows));
+    cfg->src_off = (int)off;
+    off = align16(off + (size_t)kmax * 2);
+    cfg->ray_off = (int)off;
+    off = align16(off + sizeof(RaySlotState));
+    cfg->slot_bytes = (int)off;
+    const int maxT = engine_max_threads(tsize, kmax);
+    if (n->H > maxT)
+        return fail(SRA_EUNSUPPORTED, "width %d needs %d threads per box; this K allows %d", n->rows,
+                    n->H, maxT);
+    if (cfg->slot_bytes > kMaxSmem)
+        return fail(SRA_EUNSUPPORTED, "per-box state of %d bytes exceeds shared memory", cfg->slot_bytes);
+    int NB = target_threads / n->H;
+    if (NB < 1) NB = 1;
+    while (NB > 1 && (NB * n->H > maxT || NB * cfg->slot_bytes > kMaxSmem)) --NB;
+    cfg->NB = NB;
+    return SRA_OK;
+}
+
+sra_status check_opts(const sra_opts *o) {
+    if (!o) return fail(SRA_EINVAL, "opts is NULL");
+    if (o->slope != SRA_SLOPE_CHEBYSHEV && o->slope != SRA_SLOPE_MINRANGE)
+        return fail(SRA_EINVAL, "unknown slope %d", o->slope);
+    if (o->precision < SRA_PREC_FP32 || o->precision > SRA_PREC_BF16_SOUND)
+        return fail(SRA_EINVAL, "unknown precision %d", o->precision);
+    if (o->split != SRA_SPLIT_OCTREE && o->split != SRA_SPLIT_KD)
+        return fail(SRA_EINVAL, "unknown split %d", o->split);
+    if (!(o->recheck_band >= 0.f)) return fail(SRA_EINVAL, "recheck_band must be >= 0");
+    return SRA_OK;
+}
+
+cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Keep freed stream-ordered scratch in the pool instead of returning it to
+// the driver at every synchronisation.
+void keep_pool_memory() {
+    static bool done = false;
+    if (done) return;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done = true;
+}
+
+struct Scratch {
+    void *p = nullptr;
+    cudaStream_t st = nullptr;
+    ~Scratch() {
+        if (p) cudaFreeAsync(p, st);
+    }
+};
+
+sra_status scratch_alloc(Scratch &s, size_t bytes, cudaStream_t st) {
+    keep_pool_memory();
+    s.st = st;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMallocAsync(&s.p, bytes, st);
+    if (e != cudaSuccess) {
+        s.p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? SRA_ENOMEM : SRA_ECUDA,
+                    "cudaMallocAsync(%zu): %s", bytes, cudaGetErrorString(e));
+    }
+    return SRA_OK;
+}
+
+// k-d halvings per axis at each level and the axis split when leaving it
+// (Proc. 3 widest-dimension rule, lowest axis on ties).
+void kd_tables(const float *lo, const float *hi, unsigned char n3[][3], unsigned char *axis) {
+    double e[3] = {(double)hi[0] - lo[0], (double)hi[1] - lo[1], (double)hi[2] - lo[2]};
+    int c[3] = {0, 0, 0};
+    for (int k = 0; k < kMaxKdLevels; ++k) {
+        for (int d = 0; d < 3; ++d) n3[k][d] = (unsigned char)c[d];
+        int a = 0;
+        if (e[1] > e[a]) a = 1;
+        if (e[2] > e[a]) a = 2;
+        axis[k] = (unsigned char)a;
+        e[a] *= 0.5;
+        c[a]++;
+    }
+}
+
+// Launch RangeBound over a box source in FP32 or FP64 (SIMT engine).
+sra_status run_bound(const sra_net *n, const sra_opts *o, bool fp64, int s, const BoxSrc &src,
+                     const BoundOut &out, long long n_hint, cudaStream_t st) {
+    int kmax = 0;
+    sra_status r = kmax_for(n, o, s, &kmax);
+    if (r) return r;
+    RangeCfg cfg;
+    r = make_cfg(n, o, kmax, fp64 ? 8 : 4, 256, &cfg);
+    if (r) return r;
+    long long groups = (n_hint + cfg.NB - 1) / cfg.NB;
+    long long cap = (long long)num_sms() * 64;
+    if (src.list) cap = (long long)num_sms() * 8;
+    long long grid = groups < cap ? groups : cap;
+    if (grid < 1) grid = 1;
+    cudaError_t e = fp64 ? launch_bound_f64(kmax, n->dev, src, out, cfg, grid, st)
+                         : launch_bound_f32(kmax, n->dev, src, out, cfg, grid, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "bound kernel launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+// FP32 (or FP64) bound with an optional FP64 re-check of near-zero UNKNOWNs.
+sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, BoundOut out,
+                              long long count, unsigned long long *recheck_counter,
+                              cudaStream_t st) {
+    if (o->precision == SRA_PREC_BF16_SOUND)
+        return fail(SRA_EUNSUPPORTED, "BF16-sound precision is not available for this network");
+    const bool fp64 = o->precision == SRA_PREC_FP64;
+    const bool recheck = o->recheck && !fp64;
+    Scratch sc;
+    if (recheck) {
+        sra_status r = scratch_alloc(sc, align16(sizeof(int)) + (size_t)count * sizeof(int), st);
+        if (r) return r;
+        out.flag_count = (int *)sc.p;
+        out.flag_list = (int *)((char *)sc.p + align16(sizeof(int)));
+        out.band = o->recheck_band;
+        SRA_CK(cudaMemsetAsync(out.flag_count, 0, sizeof(int), st));
+    }
+    sra_status r = run_bound(n, o, fp64, 3, src, out, count, st);
+    if (r) return r;
+    if (recheck) {
+        BoxSrc s2 = src;
+        s2.list = out.flag_list;
+        s2.list_count = out.flag_count;
+        BoundOut o2 = out;
+        o2.flag_list = nullptr;
+        o2.flag_count = nullptr;
+        o2.recheck_counter = recheck_counter;
+        r = run_bound(n, o, true, 3, s2, o2, count, st);
+        if (r) return r;
+    }
+    return SRA_OK;
+}
+
+sra_status check_net(const sra_net *n) {
+    if (!n) return fail(SRA_EINVAL, "net is NULL");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != n->device) return fail(SRA_EINVAL, "net was loaded on device %d, current is %d", n->device, dev);
+    return SRA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sra_last_error(void) { return g_err.c_str(); }
+
+void sra_default_opts(sra_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->arith = SRA_ARITH_AFFINE_FIXED;
+    o->K = 0;
+    o->slope = SRA_SLOPE_CHEBYSHEV;
+    o->precision = SRA_PREC_FP32;
+    o->recheck = 0;
+    o->recheck_band = 1e-5f;
+    o->split = SRA_SPLIT_OCTREE;
+    o->delta = 1e-3f;
+    o->t_max = 10.f;
+    o->sigma0 = 1.f;
+    o->eta_plus = 1.5f;
+    o->eta_minus = 0.5f;
+    o->safety = 0.98f;
+    o->max_iters = 1 << 20;
+}
+
+sra_status sra_load_mlp(const sra_mlp_desc *d, sra_net **out) {
+    g_err.clear();
+    if (!d || !out) return fail(SRA_EINVAL, "desc/out is NULL");
+    *out = nullptr;
+    const int L = d->n_layers;
+    if (L < 1 || L > kMaxLayers) return fail(SRA_EUNSUPPORTED, "n_layers %d outside [1, %d]", L, kMaxLayers);
+    if (!d->widths || !d->params || (L > 1 && !d->acts)) return fail(SRA_EINVAL, "null widths/acts/params");
+    if (d->pe_octaves < 0 || d->pe_octaves > 12) return fail(SRA_EINVAL, "pe_octaves %d", d->pe_octaves);
+    const int din = d->pe_octaves ? 3 + 6 * d->pe_octaves : 3;
+    if (d->widths[0] != din) return fail(SRA_EINVAL, "widths[0]=%d, expected %d", d->widths[0], din);
+    if (d->widths[L] != 1) return fail(SRA_EINVAL, "widths[n_layers] must be 1");
+    for (int l = 0; l <= L; ++l) {
+        if (d->widths[l] < 1) return fail(SRA_EINVAL, "widths[%d]=%d", l, d->widths[l]);
+        if (d->widths[l] > kMaxWidth) return fail(SRA_EUNSUPPORTED, "width %d > %d", d->widths[l], kMaxWidth);
+    }
+    for (int l = 0; l + 1 < L; ++l)
+        if (d->acts[l] < SRA_ACT_IDENTITY || d->acts[l] > SRA_ACT_SIN)
+            return fail(SRA_EINVAL, "acts[%d]=%d", l, d->acts[l]);
+    int dev = 0;
+    SRA_CK(cudaGetDevice(&dev));
+    sra_net *n = new sra_net();
+    n->device = dev;
+    n->L = L;
+    n->pe = d->pe_octaves;
+    n->din = din;
+    n->widths.assign(d->widths, d->widths + L + 1);
+    n->acts.assign(L > 1 ? d->acts : d->widths, L > 1 ? d->acts + (L - 1) : d->widths);
+    int rows = 3, hmax = din;
+    for (int l = 0; l <= L; ++l) rows = rows > d->widths[l] ? rows : d->widths[l];
+    for (int l = 1; l < L; ++l) hmax = hmax > d->widths[l] ? hmax : d->widths[l];
+    n->rows = rows;
+    n->H = ((hmax + 31) / 32) * 32;
+    n->new_syms = 6 * n->pe;
+    for (int l = 0; l + 1 < L; ++l)
+        if (n->acts[l] != SRA_ACT_IDENTITY) n->new_syms += d->widths[l + 1];
+
+    // device layout: per layer Wt (f32), b (f32), Wt64, b64; 256-byte aligned
+    std::vector<size_t> off_w(L), off_b(L), off_w64(L), off_b64(L);
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = total;
+        total += (bytes + 255) & ~size_t(255);
+        return o;
+    };
+    for (int l = 0; l < L; ++l) {
+        const size_t in = d->widths[l], o = d->widths[l + 1];
+        off_w[l] = take(in * o * 4);
+        off_b[l] = take(o * 4);
+        off_w64[l] = take(in * o * 8);
+        off_b64[l] = take(o * 8);
+    }
+    std::vector<char> host(total, 0);
+    size_t p = 0;
+    for (int l = 0; l < L; ++l) {
+        const int in = d->widths[l], o = d->widths[l + 1];
+        const float *W = d->params + p, *b = W + (size_t)in * o;
+        float *wt = (float *)(host.data() + off_w[l]);
+        double *wt64 = (double *)(host.data() + off_w64[l]);
+        for (int i = 0; i < o; ++i)
+            for (int j = 0; j < in; ++j) {
+                wt[(size_t)j * o + i] = W[(size_t)i * in + j];
+                wt64[(size_t)j * o + i] = (double)W[(size_t)i * in + j];
+            }
+        memcpy(host.data() + off_b[l], b, (size_t)o * 4);
+        double *b64 = (double *)(host.data() + off_b64[l]);
+        for (int i = 0; i < o; ++i) b64[i] = (double)b[i];
+        p += (size_t)in * o + o;
+    }
+    cudaError_t e = cudaMalloc(&n->buf, total);
+    if (e != cudaSuccess) {
+        delete n;
+        return fail(SRA_ENOMEM, "cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(n->buf, host.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(n->buf);
+        delete n;
+        return fail(SRA_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    memset(&n->dev, 0, sizeof n->dev);
+    n->dev.L = L;
+    n->dev.pe = n->pe;
+    n->dev.din = din;
+    char *base = (char *)n->buf;
+    for (int l = 0; l < L; ++l) {
+        LayerDev &ld = n->dev.layer[l];
+        ld.Wt = (const float *)(base + off_w[l]);
+        ld.b = (const float *)(base + off_b[l]);
+        ld.Wt64 = (const double *)(base + off_w64[l]);
+        ld.b64 = (const double *)(base + off_b64[l]);
+        ld.in = d->widths[l];
+        ld.out = d->widths[l + 1];
+        ld.act = (l + 1 < L) ? n->acts[l] : SRA_ACT_IDENTITY;
+    }
+    *out = n;
+    return SRA_OK;
+}
+
+sra_status sra_free_mlp(sra_net *n) {
+    if (!n) return SRA_OK;
+    cudaDeviceSynchronize();
+    if (n->buf) cudaFree(n->buf);
+    delete n;
+    return SRA_OK;
+}
+
+sra_status sra_bound_boxes(const sra_net *n, const sra_opts *o, const float *centers,
+                           const float *halfw, int64_t count, float *lo, float *hi, uint8_t *cls,
+                           void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (count < 0) return fail(SRA_EINVAL, "n < 0");
+    if (count == 0) return SRA_OK;
+    if (count > INT32_MAX) return fail(SRA_EINVAL, "n > 2^31-1");
+    if (!centers || !halfw || !cls) return fail(SRA_EINVAL, "null centers/halfw/cls");
+    BoxSrc src;
+    memset(&src, 0, sizeof src);
+    src.kind = SRC_BOXES;
+    src.centers = centers;
+    src.halfw = halfw;
+    src.n = count;
+    BoundOut out;
+    memset(&out, 0, sizeof out);
+    out.lo = lo;
+    out.hi = hi;
+    out.cls = cls;
+    return bound_with_recheck(n, o, src, out, count, nullptr, as_stream(stream));
+}
+
+sra_status sra_eval(const sra_net *n, const float *x, int64_t count, float *y, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if (count < 0 || (count > 0 && (!x || !y))) return fail(SRA_EINVAL, "bad eval arguments");
+    if (count == 0) return SRA_OK;
+    sra_opts o;
+    sra_default_opts(&o);
+    o.arith = SRA_ARITH_INTERVAL;  // zero-width intervals: exact plain forward pass
+    BoxSrc src;
+    memset(&src, 0, sizeof src);
+    src.kind = SRC_POINTS;
+    src.centers = x;
+    src.n = count;
+    BoundOut out;
+    memset(&out, 0, sizeof out);
+    out.lo = y;
+    return run_bound(n, &o, false, 1, src, out, count, as_stream(stream));
+}
+
+sra_status sra_classify_and_split(const sra_net *n, const sra_opts *o, const float *root_lo,
+                                  const float *root_hi, const sra_node *in, int64_t n_in,
+                                  int32_t max_level, sra_node *out, int64_t cap_out,
+                                  sra_node *leaves, int64_t cap_leaves, int64_t *counts,
+                                  void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (!root_lo || !root_hi || !counts) return fail(SRA_EINVAL, "null root/counts");
+    for (int d = 0; d < 3; ++d)
+        if (!(root_hi[d] > root_lo[d])) return fail(SRA_EINVAL, "empty root box on axis %d", d);
+    const int lvl_cap = (o->split == SRA_SPLIT_OCTREE) ? 16 : kMaxKdLevels - 1;
+    if (max_level < 0 || max_level > lvl_cap) return fail(SRA_EINVAL, "max_level %d outside [0, %d]", max_level, lvl_cap);
+    if (n_in < 0 || cap_out < 0 || cap_leaves < 0) return fail(SRA_EINVAL, "negative size");
+    if (n_in > INT32_MAX) return fail(SRA_EINVAL, "n_in > 2^31-1");
+    if (n_in > 0 && !in) return fail(SRA_EINVAL, "null frontier_in");
+    if ((cap_out > 0 && !out) || (cap_leaves > 0 && !leaves)) return fail(SRA_EINVAL, "null output buffer");
+    if (n_in == 0) return SRA_OK;
+    cudaStream_t st = as_stream(stream);
+
+    BoxSrc src;
+    memset(&src, 0, sizeof src);
+    src.kind = SRC_NODES;
+    src.nodes = in;
+    src.n = n_in;
+    src.split = o->split;
+    unsigned char axis[kMaxKdLevels];
+    kd_tables(root_lo, root_hi, src.kd_n3, axis);
+    for (int d = 0; d < 3; ++d) {
+        src.root_lo[d] = root_lo[d];
+        src.root_ext[d] = root_hi[d] - root_lo[d];
+    }
+    const long long nblk = split_blocks(n_in);
+    Scratch sc;
+    const size_t cls_bytes = align16((size_t)n_in), blk_bytes = align16((size_t)nblk * 2 * 8);
+    if ((r = scratch_alloc(sc, cls_bytes + blk_bytes, st))) return r;
+    uint8_t *cls = (uint8_t *)sc.p;
+    long long *blk = (long long *)((char *)sc.p + cls_bytes);
+
+    BoundOut bo;
+    memset(&bo, 0, sizeof bo);
+    bo.cls = cls;
+    if ((r = bound_with_recheck(n, o, src, bo, n_in,
+                                (unsigned long long *)(counts + SRA_CNT_RECHECKED), st)))
+        return r;
+    SplitArgs a;
+    memset(&a, 0, sizeof a);
+    a.cls = cls;
+    a.in = in;
+    a.n = n_in;
+    a.max_level = max_level;
+    a.split = o->split;
+    memcpy(a.kd_axis, axis, sizeof axis);
+    a.out = out;
+    a.cap_out = cap_out;
+    a.leaves = leaves;
+    a.cap_leaves = cap_leaves;
+    a.counts = (unsigned long long *)counts;
+    a.blk = blk;
+    cudaError_t e = launch_split(a, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "split launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origins,
+                         const float *dirs, int64_t count, float *t_hit, int32_t *iters,
+                         void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (count < 0) return fail(SRA_EINVAL, "n < 0");
+    if (count == 0) return SRA_OK;
+    if (!origins || !dirs || !t_hit) return fail(SRA_EINVAL, "null origins/dirs/t_hit");
+    if (!(o->delta > 0.f) || !(o->t_max > 0.f) || !(o->sigma0 > 0.f) || !(o->eta_plus >= 1.f) ||
+        !(o->eta_minus > 0.f && o->eta_minus < 1.f) || !(o->safety > 0.f && o->safety <= 1.f) ||
+        o->max_iters < 1)
+        return fail(SRA_EINVAL, "ray options out of range (delta, t_max, sigma0 > 0; eta+ >= 1; "
+                                "0 < eta- < 1; 0 < safety <= 1; max_iters >= 1)");
+    if (o->precision != SRA_PREC_FP32)
+        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32");
+    cudaStream_t st = as_stream(stream);
+    Scratch sc;
+    const size_t f0_bytes = align16((size_t)count * 4);
+    if ((r = scratch_alloc(sc, f0_bytes + 16, st))) return r;
+    float *f0 = (float *)sc.p;
+    unsigned long long *next = (unsigned long long *)((char *)sc.p + f0_bytes);
+    // f(p) at every origin: the reference sign of DifferentSigns (Proc. 2)
+    if ((r = sra_eval(n, origins, count, f0, stream))) return r;
+    SRA_CK(cudaMemsetAsync(next, 0, 8, st));
+    int kmax = 0;
+    if ((r = kmax_for(n, o, 1, &kmax))) return r;
+    RangeCfg cfg;
+    if ((r = make_cfg(n, o, kmax, 4, 512, &cfg))) return r;
+    RayParams rp;
+    memset(&rp, 0, sizeof rp);
+    rp.origins = origins;
+    rp.dirs = dirs;
+    rp.f0 = f0;
+    rp.t_hit = t_hit;
+    rp.iters = iters;
+    rp.n = count;
+    rp.next = next;
+    rp.delta = o->delta;
+    rp.t_max = o->t_max;
+    rp.sigma0 = o->sigma0;
+    rp.eta_plus = o->eta_plus;
+    rp.eta_minus = o->eta_minus;
+    rp.safety = o->safety;
+    rp.max_iters = o->max_iters;
+    const int per_sm = rays_blocks_per_sm_f32(kmax, cfg);
+    long long grid = (long long)per_sm * num_sms();
+    const long long need = (count + cfg.NB - 1) / cfg.NB;
+    if (grid > need) grid = need;
+    cudaError_t e = launch_rays_f32(kmax, n->dev, &rp, cfg, (int)grid, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "ray kernel launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *xl, const float *xu,
+                              int32_t depth, sra_node *leaves, int64_t cap, int64_t *n_leaves,
+                              int64_t *level_counts, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (!xl || !xu || !n_leaves) return fail(SRA_EINVAL, "null xl/xu/n_leaves");
+    if (cap < 0 || (cap > 0 && !leaves)) return fail(SRA_EINVAL, "bad leaves buffer");
+    cudaStream_t st = as_stream(stream);
+    const int fan = (o->split == SRA_SPLIT_OCTREE) ? 8 : 2;
+    int64_t *dcounts = nullptr;
+    sra_node *bufA = nullptr, *bufB = nullptr;
+    size_t capA = 0, capB = 0;
+    sra_status status = SRA_OK;
+    int64_t hc[SRA_CNT_N] = {0};
+    long long ncur = 1;
+    keep_pool_memory();
+    auto grow = [&](sra_node **b, size_t *c, size_t need) -> sra_status {
+        if (need <= *c) return SRA_OK;
+        if (*b) cudaFreeAsync(*b, st);
+        *b = nullptr;
+        size_t want = need < 1024 ? 1024 : need;
+        cudaError_t e = cudaMallocAsync((void **)b, want * sizeof(sra_node), st);
+        if (e != cudaSuccess) {
+            *b = nullptr;
+            *c = 0;
+            return fail(SRA_ENOMEM, "frontier buffer of %zu nodes: %s", want, cudaGetErrorString(e));
+        }
+        *c = want;
+        return SRA_OK;
+    };
+    cudaError_t e = cudaMallocAsync((void **)&dcounts, SRA_CNT_N * sizeof(int64_t), st);
+    if (e != cudaSuccess) return fail(SRA_ENOMEM, "counts: %s", cudaGetErrorString(e));
+    if ((status = grow(&bufA, &capA, 1)) == SRA_OK) {
+        sra_node root = {0, 0, 0, 0};
+        e = cudaMemcpyAsync(bufA, &root, sizeof root, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) status = fail(SRA_ECUDA, "root upload: %s", cudaGetErrorString(e));
+        // the host copy must stay valid until the copy ran
+        if (status == SRA_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            status = fail(SRA_ECUDA, "stream sync");
+    }
+    for (int level = 0; status == SRA_OK && level <= depth; ++level) {
+        const size_t next = (level < depth) ? (size_t)ncur * fan : 0;
+        if ((status = grow(&bufB, &capB, next > 0 ? next : 1)) != SRA_OK) break;
+        e = cudaMemsetAsync(dcounts, 0, SRA_CNT_N * sizeof(int64_t), st);
+        if (e != cudaSuccess) { status = fail(SRA_ECUDA, "memset: %s", cudaGetErrorString(e)); break; }
+        status = sra_classify_and_split(n, o, xl, xu, bufA, ncur, depth, bufB, (int64_t)next,
+                                        leaves, cap, dcounts, stream);
+        if (status) break;
+        e = cudaMemcpyAsync(hc, dcounts, sizeof hc, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { status = fail(SRA_ECUDA, "level %d: %s", level, cudaGetErrorString(e)); break; }
+        if (level_counts) {
+            level_counts[level * 3 + 0] = hc[SRA_CNT_POSITIVE];
+            level_counts[level * 3 + 1] = hc[SRA_CNT_NEGATIVE];
+            level_counts[level * 3 + 2] = hc[SRA_CNT_UNKNOWN];
+        }
+        ncur = hc[SRA_CNT_CHILDREN];
+        std::swap(bufA, bufB);
+        std::swap(capA, capB);
+        if (ncur == 0 && level < depth) {
+            for (int k = level + 1; level_counts && k <= depth; ++k)
+                level_counts[k * 3 + 0] = level_counts[k * 3 + 1] = level_counts[k * 3 + 2] = 0;
+            hc[SRA_CNT_LEAVES] = 0;
+            break;
+        }
+    }
+    if (bufA) cudaFreeAsync(bufA, st);
+    if (bufB) cudaFreeAsync(bufB, st);
+    cudaFreeAsync(dcounts, st);
+    if (status) return status;
+    *n_leaves = hc[SRA_CNT_LEAVES];
+    if (hc[SRA_CNT_LEAVES] > cap)
+        return fail(SRA_ECAPACITY, "%lld leaves, capacity %lld", (long long)hc[SRA_CNT_LEAVES], (long long)cap);
+    return SRA_OK;
+}
+
+}  // extern "C"

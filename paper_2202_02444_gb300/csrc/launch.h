@@ -1,0 +1,43 @@
+// Host-side launch interface between the C-ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sra_common.cuh"
+
+namespace sra {
+
+__host__ __device__ constexpr int engine_row_stride(int kmax) { return ((kmax + 3 + 3) / 4) * 4; }
+
+// KMAX values the engine is instantiated for.
+constexpr int kKmaxList[] = {1, 4, 8, 16, 32, 64, 128};
+
+cudaError_t launch_bound_f32(int kmax, const NetDev &net, const BoxSrc &src, const BoundOut &out,
+                             const RangeCfg &cfg, long long grid, cudaStream_t st);
+cudaError_t launch_bound_f64(int kmax, const NetDev &net, const BoxSrc &src, const BoundOut &out,
+                             const RangeCfg &cfg, long long grid, cudaStream_t st);
+
+struct RayParams;
+cudaError_t launch_rays_f32(int kmax, const NetDev &net, const void *rp, const RangeCfg &cfg,
+                            int grid, cudaStream_t st);
+int rays_blocks_per_sm_f32(int kmax, const RangeCfg &cfg);
+
+// Frontier round (Proc. 3 split) after classification.
+struct SplitArgs {
+    const uint8_t *cls;
+    const sra_node *in;
+    long long n;
+    int max_level;
+    int split;                           // SRA_SPLIT_*
+    unsigned char kd_axis[kMaxKdLevels]; // k-d split axis leaving each level
+    sra_node *out;
+    long long cap_out;
+    sra_node *leaves;
+    long long cap_leaves;
+    unsigned long long *counts;          // device int64[SRA_CNT_N]
+    long long *blk;                      // scratch: 2 * nblocks
+};
+cudaError_t launch_split(const SplitArgs &a, cudaStream_t st);
+long long split_blocks(long long n);
+
+}  // namespace sra
