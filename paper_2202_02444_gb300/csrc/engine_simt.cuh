@@ -111,9 +111,7 @@ __device__ __forceinline__ void matmul_row(const LayerDev &L, const T *X, int i,
     r.p = T(0);
     Dot2<T> cd;
     const int in = L.in, out = L.out;
-#pragma unroll 2
-    for (int j = 0; j < in; ++j) {
-        const T w = __ldg(Wt + (size_t)j * out + i);
+    auto step = [&](T w, int j) {
         const T aw = fabs(w);
         const T *xr = X + j * RS;
 #pragma unroll
@@ -122,7 +120,18 @@ __device__ __forceinline__ void matmul_row(const LayerDev &L, const T *X, int i,
         else r.c = fma(w, xr[KMAX], r.c);
         r.xi = fma(aw, xr[KMAX + 1], r.xi);
         if (PT) r.p = fma(w, xr[KMAX + 2], r.p);
+    };
+    // weights of 8 inputs in flight before their FMAs (latency of L2 loads)
+    constexpr int U = 8;
+    int j = 0;
+    for (; j + U <= in; j += U) {
+        T w[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) w[q] = __ldg(Wt + (size_t)(j + q) * out + i);
+#pragma unroll
+        for (int q = 0; q < U; ++q) step(w[q], j + q);
     }
+    for (; j < in; ++j) step(__ldg(Wt + (size_t)j * out + i), j);
     const T bias = __ldg(b_of<T>(L) + i);
     if (COMP) {
         cd.add(bias);
@@ -252,6 +261,8 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
 
 // Positional encoding rows (sin / cos of 2^k pi x) as a nonlinearity layer
 // over the 3 input rows: rows 0..2 identity, then per octave 3 sin + 3 cos.
+// Each row works on t = 2^k x (+1/2 for cos) in half-turns, which is exact,
+// and applies the sin(pi t) rule.
 template <typename T, int KMAX, bool PT>
 __device__ int posenc_layer(const NetDev &net, const RangeCfg &cfg, const Slot<T> &s, int i, int Ncur) {
     constexpr int RS = RowStride<KMAX>::value;
@@ -268,15 +279,34 @@ __device__ int posenc_layer(const NetDev &net, const RangeCfg &cfg, const Slot<T
             is_cos = (q % 6) >= 3;
             d = q % 3;
         }
-        const T sc = (k < 0) ? T(1) : Num<T>::pi() * T(1 << k);
-        const T sh = is_cos ? T(0.5) * Num<T>::pi() : T(0);
+        const T sc = (k < 0) ? T(1) : T(1 << k);
+        const T sh = is_cos ? T(0.5) : T(0);
         const T *xr = s.X + d * RS;
 #pragma unroll
         for (int q = 0; q < KMAX; ++q) r.a[q] = sc * xr[q];
         r.c = sc * xr[KMAX] + sh;
-        r.xi = fabs(sc) * xr[KMAX + 1];
+        r.xi = sc * xr[KMAX + 1];
         r.p = sc * xr[KMAX + 2] + sh;
-        if (k >= 0) gamma = activate_row<T, KMAX, PT>(SRA_ACT_SIN, cfg, r);
+        if (k >= 0) {
+            if (cfg.arith == SRA_ARITH_INTERVAL) {
+                T lo, hi;
+                sinpi_extremes<T>(r.c - r.xi, r.c + r.xi, lo, hi);
+                r.c = T(0.5) * (lo + hi);
+                r.xi = T(0.5) * (hi - lo);
+            } else {
+                T rad = T(0);
+#pragma unroll
+                for (int q = 0; q < KMAX; ++q) rad += fabs(r.a[q]);
+                rad += r.xi;
+                T a, b;
+                linearize_sinpi<T>(r.c - rad, r.c + rad, a, b, gamma);
+#pragma unroll
+                for (int q = 0; q < KMAX; ++q) r.a[q] *= a;
+                r.c = a * r.c + b;
+                r.xi = fabs(a) * r.xi;
+            }
+            if (PT) r.p = sinpi_t(r.p);
+        }
     }
     __syncthreads();  // every read of the input rows is done
     return condense_and_store<T, KMAX, PT>(r, gamma, valid, i >= 3, i - 3, 6 * net.pe, Ncur, cfg, s, i);

@@ -234,6 +234,56 @@ __device__ __forceinline__ void linearize(int act, int slope, T l, T u, T &a, T 
     }
 }
 
+__device__ __forceinline__ float sinpi_t(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_t(double x) { return sinpi(x); }
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+
+// The sin rule for y = sin(pi t) on t in [l,u] (t in half-turns), used by the
+// positional encoding sin(2^k pi x) = sin(pi * 2^k x): 2^k x is exact, so the
+// argument carries no rounding of pi even where 2^k pi x is large. Same rule
+// as `linearize` for sin (slope from the cos range, extremes of
+// g(t) = sin(pi t) - a t at the ends and at the extreme critical points),
+// with the slope a expressed per unit of t.
+template <typename T>
+__device__ __forceinline__ void linearize_sinpi(T l, T u, T &a, T &b, T &g) {
+    if (u - l >= T(2)) { a = T(0); b = T(0); g = T(1); return; }
+    // extremes of cos(pi t) on [l,u]: +1 at even integers, -1 at odd ones
+    const T cl = cospi_t(l), cu = cospi_t(u);
+    T chi = fmax(cl, cu), clo = fmin(cl, cu);
+    if (T(2) * ceil(l / T(2)) <= u) chi = T(1);
+    if (T(2) * ceil((l - T(1)) / T(2)) + T(1) <= u) clo = T(-1);
+    const T az = (clo + chi) / T(2);  // slope per radian
+    a = az * Num<T>::pi();            // slope per half-turn
+    const T e = acos(clampT<T>(az, T(-1), T(1))) / Num<T>::pi();
+    T cand[5];
+    cand[0] = u;
+    cand[1] = clampT<T>(e + T(2) * ceil((l - e) / T(2)), l, u);
+    cand[2] = clampT<T>(e + T(2) * floor((u - e) / T(2)), l, u);
+    cand[3] = clampT<T>(-e + T(2) * ceil((l + e) / T(2)), l, u);
+    cand[4] = clampT<T>(-e + T(2) * floor((u + e) / T(2)), l, u);
+    T dmax = T(0), dmin = T(0);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        const T h = T(0.5) * (cand[q] - l);
+        const T d = T(2) * cospi_t(l + h) * sinpi_t(h) - a * (cand[q] - l);
+        dmax = fmax(dmax, d);
+        dmin = fmin(dmin, d);
+    }
+    g = T(0.5) * (dmax - dmin);
+    b = (sinpi_t(l) - a * l) + T(0.5) * (dmax + dmin);
+}
+
+// Interval image of sin(pi t) on [l,u].
+template <typename T> __device__ __forceinline__ void sinpi_extremes(T l, T u, T &lo, T &hi) {
+    if (u - l >= T(2)) { lo = T(-1); hi = T(1); return; }
+    const T sl = sinpi_t(l), su = sinpi_t(u);
+    hi = fmax(sl, su);
+    lo = fmin(sl, su);
+    if (T(2) * ceil((l - T(0.5)) / T(2)) + T(0.5) <= u) hi = T(1);
+    if (T(2) * ceil((l + T(0.5)) / T(2)) - T(0.5) <= u) lo = T(-1);
+}
+
 __device__ __forceinline__ int classify_range(float lo, float hi) {
     return lo > 0.f ? SRA_POSITIVE : (hi < 0.f ? SRA_NEGATIVE : SRA_UNKNOWN);
 }
