@@ -200,6 +200,31 @@ sra_status sra_extract_leaves(const sra_net *net, const sra_opts *opts, const fl
  * float[n]) in the network's FP32 weights. Asynchronous. */
 sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, void *stream);
 
+/* Allocation-free variant of sra_classify_and_split (same arguments, same
+ * results). The paper has no counterpart: it exists for callers that cannot
+ * allocate device memory at all, such as code running inside a captured CUDA
+ * graph whose memory plan is fixed, real-time loops that forbid allocator
+ * calls and their implicit synchronisation on the hot path, or hosts that
+ * give this library a pre-partitioned device without an allocator. The round's
+ * scratch lives in a fixed file-scope device array of
+ * SRA_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; the call itself allocates nothing.
+ * Limits: n_in <= SRA_NOALLOC_MAX_NODES, else SRA_EINVAL (nothing queued);
+ * precision FP32 or FP64 (BF16_SOUND gives SRA_EUNSUPPORTED).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture. All calls share
+ * the array, which keeps the previous call's contents (each call clears what
+ * must start at zero): calls whose device work overlaps (other streams or
+ * host threads) race on it, so serialise them. Asynchronous on `stream`. */
+#define SRA_NOALLOC_MAX_NODES 524288
+#define SRA_NOALLOC_SCRATCH_BYTES (5u << 20)
+sra_status sra_classify_and_split_noalloc(const sra_net *net, const sra_opts *opts,
+                                          const float *root_lo, const float *root_hi,
+                                          const sra_node *frontier_in, int64_t n_in,
+                                          int32_t max_level, sra_node *frontier_out,
+                                          int64_t cap_out, sra_node *leaves_out,
+                                          int64_t cap_leaves, int64_t *counts, void *stream);
+
 /* Description of the last error on this thread ("" if none). */
 const char *sra_last_error(void);
 

@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -619,3 +620,148 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of sra_classify_and_split.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// captured CUDA graph whose memory plan is fixed, real-time render or serving
+// loops that forbid allocator calls (and their implicit synchronisation) on
+// the hot path, and hosts that hand this library a pre-partitioned device
+// with no allocator of their own. For them the scratch this round needs
+// (per-node classes, per-block scan totals, the re-check list) lives in one
+// file-scope __device__ array of fixed size instead of cudaMallocAsync memory.
+//
+// Limits and contract (also in include/sra.h):
+//   - n_in <= SRA_NOALLOC_MAX_NODES (524288 nodes per call); larger inputs are
+//     rejected with SRA_EINVAL before any device work is queued.
+//   - The array is shared by every call in the process on a given device:
+//     calls whose device work overlaps (two streams, or two host threads)
+//     race on it and give undefined results. Serialise them.
+//   - The array keeps the last call's contents; each call clears the one
+//     field that must start at zero (the re-check counter) itself.
+//   - The first call on each device resolves the array's device address with
+//     cudaGetSymbolAddress (a host-side name of a __device__ variable is not a
+//     device address). Make that first call before any stream capture.
+//   - The array occupies SRA_NOALLOC_SCRATCH_BYTES of device memory on every
+//     GPU that loads this library, until the process exits.
+namespace {
+
+constexpr size_t kNoallocCls = (size_t)SRA_NOALLOC_MAX_NODES;                  // uint8 per node
+constexpr size_t kNoallocBlk = ((SRA_NOALLOC_MAX_NODES + 1023) / 1024) * 2 * 8; // scan totals
+constexpr size_t kNoallocFlags = 16 + (size_t)SRA_NOALLOC_MAX_NODES * 4;       // count + list
+static_assert(kNoallocCls + kNoallocBlk + kNoallocFlags <= SRA_NOALLOC_SCRATCH_BYTES,
+              "scratch array too small for its node limit");
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SRA_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array on the current device (once per device).
+sra_status noalloc_scratch(void **out) {
+    int dev = 0;
+    SRA_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SRA_EUNSUPPORTED, "device ordinal %d", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SRA_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return SRA_OK;
+}
+
+}  // namespace
+
+extern "C" sra_status sra_classify_and_split_noalloc(
+    const sra_net *n, const sra_opts *o, const float *root_lo, const float *root_hi,
+    const sra_node *in, int64_t n_in, int32_t max_level, sra_node *out, int64_t cap_out,
+    sra_node *leaves, int64_t cap_leaves, int64_t *counts, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (!root_lo || !root_hi || !counts) return fail(SRA_EINVAL, "null root/counts");
+    for (int d = 0; d < 3; ++d)
+        if (!(root_hi[d] > root_lo[d])) return fail(SRA_EINVAL, "empty root box on axis %d", d);
+    const int lvl_cap = (o->split == SRA_SPLIT_OCTREE) ? 16 : kMaxKdLevels - 1;
+    if (max_level < 0 || max_level > lvl_cap)
+        return fail(SRA_EINVAL, "max_level %d outside [0, %d]", max_level, lvl_cap);
+    if (n_in < 0 || cap_out < 0 || cap_leaves < 0) return fail(SRA_EINVAL, "negative size");
+    if (n_in > SRA_NOALLOC_MAX_NODES)
+        return fail(SRA_EINVAL, "n_in %lld exceeds the allocation-free limit of %d nodes per call",
+                    (long long)n_in, SRA_NOALLOC_MAX_NODES);
+    if (n_in > 0 && !in) return fail(SRA_EINVAL, "null frontier_in");
+    if ((cap_out > 0 && !out) || (cap_leaves > 0 && !leaves)) return fail(SRA_EINVAL, "null output buffer");
+    if (o->precision == SRA_PREC_BF16_SOUND)
+        return fail(SRA_EUNSUPPORTED, "the allocation-free round runs in FP32 or FP64");
+    void *scratch = nullptr;
+    if ((r = noalloc_scratch(&scratch))) return r;  // before any early return for n_in == 0
+    if (n_in == 0) return SRA_OK;
+    cudaStream_t st = as_stream(stream);
+
+    uint8_t *cls = (uint8_t *)scratch;
+    long long *blk = (long long *)((char *)scratch + kNoallocCls);
+    int *flag_count = (int *)((char *)scratch + kNoallocCls + kNoallocBlk);
+    int *flag_list = (int *)((char *)scratch + kNoallocCls + kNoallocBlk + 16);
+
+    BoxSrc src;
+    memset(&src, 0, sizeof src);
+    src.kind = SRC_NODES;
+    src.nodes = in;
+    src.n = n_in;
+    src.split = o->split;
+    unsigned char axis[kMaxKdLevels];
+    kd_tables(root_lo, root_hi, src.kd_n3, axis);
+    for (int d = 0; d < 3; ++d) {
+        src.root_lo[d] = root_lo[d];
+        src.root_ext[d] = root_hi[d] - root_lo[d];
+    }
+    const bool fp64 = o->precision == SRA_PREC_FP64;
+    const bool recheck = o->recheck && !fp64;
+    BoundOut bo;
+    memset(&bo, 0, sizeof bo);
+    bo.cls = cls;
+    if (recheck) {
+        bo.flag_count = flag_count;
+        bo.flag_list = flag_list;
+        bo.band = o->recheck_band;
+        SRA_CK(cudaMemsetAsync(flag_count, 0, sizeof(int), st));  // must start at zero
+    }
+    if ((r = run_bound(n, o, fp64, 3, src, bo, n_in, st))) return r;
+    if (recheck) {
+        BoxSrc s2 = src;
+        s2.list = flag_list;
+        s2.list_count = flag_count;
+        BoundOut o2 = bo;
+        o2.flag_list = nullptr;
+        o2.flag_count = nullptr;
+        o2.recheck_counter = (unsigned long long *)(counts + SRA_CNT_RECHECKED);
+        if ((r = run_bound(n, o, true, 3, s2, o2, n_in, st))) return r;
+    }
+    SplitArgs a;
+    memset(&a, 0, sizeof a);
+    a.cls = cls;
+    a.in = in;
+    a.n = n_in;
+    a.max_level = max_level;
+    a.split = o->split;
+    memcpy(a.kd_axis, axis, sizeof axis);
+    a.out = out;
+    a.cap_out = cap_out;
+    a.leaves = leaves;
+    a.cap_leaves = cap_leaves;
+    a.counts = (unsigned long long *)counts;
+    a.blk = blk;
+    cudaError_t e = launch_split(a, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "split launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
