@@ -69,6 +69,16 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+__device__ __forceinline__ void load4(const float *p, float *v) {
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double *p, double *v) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // Round-to-nearest add / multiply that the compiler may not fuse into an FMA
 // (error-free transformations depend on each operation rounding once).
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
@@ -113,13 +123,31 @@ __device__ __forceinline__ void matmul_row(const LayerDev &L, const T *X, int i,
     const int in = L.in, out = L.out;
     auto step = [&](T w, int j) {
         const T aw = fabs(w);
-        const T *xr = X + j * RS;
+        const T *xr = X + j * RS;  // 16-byte aligned: RS is a multiple of 4
+        // broadcast 16-byte loads (every lane of the warp reads the same row)
+        constexpr int K4 = (KMAX + 3) / 4;
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) r.a[k] = fma(w, xr[k], r.a[k]);
-        if (COMP) cd.add_prod(w, xr[KMAX]);
-        else r.c = fma(w, xr[KMAX], r.c);
-        r.xi = fma(aw, xr[KMAX + 1], r.xi);
-        if (PT) r.p = fma(w, xr[KMAX + 2], r.p);
+        for (int q = 0; q < K4; ++q) {
+            T v[4];
+            load4(xr + 4 * q, v);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 4 * q + e;
+                if (k < KMAX) r.a[k] = fma(w, v[e], r.a[k]);
+                else if (k == KMAX) { if (COMP) cd.add_prod(w, v[e]); else r.c = fma(w, v[e], r.c); }
+                else if (k == KMAX + 1) r.xi = fma(aw, v[e], r.xi);
+                else if (k == KMAX + 2) { if (PT) r.p = fma(w, v[e], r.p); }
+            }
+        }
+        if (KMAX % 4 == 0) {  // c, xinf, p sit in the next 16 bytes
+            T v[4];
+            load4(xr + KMAX, v);
+            if (COMP) cd.add_prod(w, v[0]);
+            else r.c = fma(w, v[0], r.c);
+            r.xi = fma(aw, v[1], r.xi);
+            if (PT) r.p = fma(w, v[2], r.p);
+        } else if (KMAX % 4 == 1) {  // KMAX == 1: [A0, c, xinf, p] was one load
+        }
     };
     // weights of 8 inputs in flight before their FMAs (latency of L2 loads)
     constexpr int U = 8;
@@ -298,12 +326,16 @@ __device__ int posenc_layer(const NetDev &net, const RangeCfg &cfg, const Slot<T
 #pragma unroll
                 for (int q = 0; q < KMAX; ++q) rad += fabs(r.a[q]);
                 rad += r.xi;
-                T a, b;
-                linearize_sinpi<T>(r.c - rad, r.c + rad, a, b, gamma);
+                // The encoding rows are few (6 per octave); their rule runs in
+                // FP64 from the exact (c, rad): an FP32 c - rad would lose the
+                // width of a narrow range, to which gamma is quadratic.
+                double a, b, g;
+                linearize_sinpi<double>((double)r.c - (double)rad, (double)r.c + (double)rad, a, b, g);
 #pragma unroll
-                for (int q = 0; q < KMAX; ++q) r.a[q] *= a;
-                r.c = a * r.c + b;
-                r.xi = fabs(a) * r.xi;
+                for (int q = 0; q < KMAX; ++q) r.a[q] *= T(a);
+                r.c = T(a * (double)r.c + b);
+                r.xi = T(fabs(a)) * r.xi;
+                gamma = T(g);
             }
             if (PT) r.p = sinpi_t(r.p);
         }

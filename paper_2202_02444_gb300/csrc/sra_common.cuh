@@ -182,10 +182,11 @@ __device__ __forceinline__ void linearize(int act, int slope, T l, T u, T &a, T 
         if (l >= T(0)) return;
         const T fl = expm1(l);
         // f(u) - f(l) without cancellation
-        const T df = (u > T(0)) ? (u - fl) : exp(l) * expm1(u - l);
+        // (exp(l) expm1(u - l) would be 0 * inf for very wide negative ranges)
+        const T df = (u > T(0)) ? (u - fl) : ((u - l < T(30)) ? exp(l) * expm1(u - l) : expm1(u) - fl);
         if (slope == SRA_SLOPE_MINRANGE) {
             a = exp(l);  // smallest derivative: f - a x is non-decreasing on [l,u]
-            const T spread = (u > T(0)) ? (df - a * (u - l)) : a * expm1_minus_id<T>(u - l);
+            const T spread = (u > T(0) || u - l >= T(30)) ? (df - a * (u - l)) : a * expm1_minus_id<T>(u - l);
             g = T(0.5) * spread;
             b = (fl - a * l) + g;
             return;
