@@ -62,7 +62,8 @@ def parse_args():
     ap.add_argument("--ray-iters", type=int, default=1500, help="per-ray iteration cap of the ray phase")
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=48, help="oracle boxes for cpu_baseline")
+    ap.add_argument("--cpu-sample", type=int, default=2048, help="oracle boxes for cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
     return ap.parse_args()
 
 
