@@ -62,6 +62,8 @@ def parse_args():
     ap.add_argument("--ray-iters", type=int, default=1500, help="per-ray iteration cap of the ray phase")
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--kernel-case", default=None, choices=["fp32", "bf16_sound", "bf16", "fp64"],
+                    help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="oracle boxes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
     return ap.parse_args()
@@ -192,8 +194,27 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def kernel_case(args):
+    """The dominant kernel alone, for profilers: two sra_bound_boxes calls on
+    --batch boxes (half-widths log-uniform in [1/1024, 1/64]) of the
+    3-[256]x8-1 ReLU net, affine-truncate K=64, in the given precision."""
+    import torch
+    from paper_2202_02444_gb300 import sra
+    net = sra.Net(wl.net_relu256x8())
+    c, h = wl.make_boxes(args.batch, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
+    C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
+    o = sra.make_opts(arith="truncate", K=64, precision=args.kernel_case)
+    for _ in range(2):
+        sra.bound_boxes(net, C_, H_, opts=o)
+    torch.cuda.synchronize()
+    print("kernel case done", args.kernel_case, args.batch)
+
+
 def main():
     args = parse_args()
+    if args.kernel_case:
+        kernel_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return

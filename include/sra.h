@@ -58,14 +58,24 @@ enum {
 enum { SRA_SLOPE_CHEBYSHEV = 0, SRA_SLOPE_MINRANGE = 1 };
 
 /* Arithmetic the bound is computed in.
- *   FP32:       plain single precision, no rounding control (the paper's form,
- *               which Sec. 3.4 states needs none in practice).
+ *   FP32:       plain single precision, no rounding control (the paper's form;
+ *               Sec. 3.4 reports that none was needed in practice).
  *   FP64:       plain double precision.
- *   BF16_SOUND: noise-symbol products on BF16 tensor cores with FP32
- *               accumulation, center and x_inf in FP32, and an a-priori
- *               rounding radius folded into x_inf so the bound stays
- *               guaranteed (outward-rounded range). */
-enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2 };
+ *   BF16_SOUND: the dense layers on BF16 tensor cores with FP32 accumulation
+ *               (weights split into a BF16 hi/lo pair, centers as a BF16
+ *               hi/lo pair), and an a-priori rounding radius of every FP
+ *               operation folded into x_inf with outward rounding, so the
+ *               range is guaranteed to contain f over the box. The radius
+ *               sits in x_inf, which every later layer widens by the row sums
+ *               of |W|: on deep wide networks the bound is much wider than the
+ *               exact-arithmetic affine bound.
+ *   BF16:       the same tensor-core computation without the rounding radius
+ *               (plain, like FP32; results differ from FP64 by BF16 operand
+ *               rounding of the noise columns).
+ * BF16_SOUND and BF16 serve 3 -> H x L -> 1 ReLU networks (H = 128 or 256, up
+ * to 12 hidden layers) with affine-truncate K = 64; other shapes return
+ * SRA_EUNSUPPORTED. */
+enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2, SRA_PREC_BF16 = 3 };
 
 /* Tree refinement: 8-way octree (one level = 3 k-d levels on a cube) or the
  * widest-axis binary split of Proc. 3 ("BuildSpatialTree"). */
@@ -224,6 +234,20 @@ sra_status sra_classify_and_split_noalloc(const sra_net *net, const sra_opts *op
                                           int32_t max_level, sra_node *frontier_out,
                                           int64_t cap_out, sra_node *leaves_out,
                                           int64_t cap_leaves, int64_t *counts, void *stream);
+
+/* Diagnostics: self-test of the tensor-core building blocks used by
+ * SRA_PREC_BF16_SOUND (TMA-loaded 128-byte-swizzled K-major weight tiles,
+ * thread-written operand tiles, tcgen05.mma into TMEM, tcgen05.ld). Computes
+ * D[256][144] = W[256][256] * X[144][256]^T with W, X device bf16 row-major
+ * and D device float; *status (device int, zero it first) becomes non-zero if
+ * a bounded wait ran out. Asynchronous; one CTA. */
+sra_status sra_selftest_tc_gemm(const void *W, const void *X, float *D, int *status, void *stream);
+
+/* Synchronise `stream` and report kernel-side failures recorded for this
+ * network since the last call: SRA_ETIMEOUT if a bounded device wait of the
+ * tensor-core path ran out (the kernel then left without finishing its boxes;
+ * their outputs are undefined). The record is cleared. */
+sra_status sra_sync_status(const sra_net *net, void *stream);
 
 /* Description of the last error on this thread ("" if none). */
 const char *sra_last_error(void);

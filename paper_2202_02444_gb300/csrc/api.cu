@@ -4,12 +4,15 @@
 // kernels of this library.
 #include <cstdarg>
 #include <cstdio>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
 
 #include "launch.h"
+#include "tc_bound.h"
+#include "tc_host.h"
 
 using namespace sra;
 
@@ -22,6 +25,11 @@ struct sra_net {
     int new_syms = 0;  // symbols created by all nonlinearities (affine-full sizing)
     void *buf = nullptr;
     int device = 0;
+    // BF16-sound tensor-core path (3 -> H x (L-1) -> 1 ReLU nets, H = 128/256)
+    bool tc_ok = false;
+    int tc_H = 0;
+    void *tc_buf = nullptr;  // bf16 hi/lo weights of the hidden layers, status word
+    TcParams tcp;
 };
 
 namespace {
@@ -115,7 +123,7 @@ sra_status check_opts(const sra_opts *o) {
     if (!o) return fail(SRA_EINVAL, "opts is NULL");
     if (o->slope != SRA_SLOPE_CHEBYSHEV && o->slope != SRA_SLOPE_MINRANGE)
         return fail(SRA_EINVAL, "unknown slope %d", o->slope);
-    if (o->precision < SRA_PREC_FP32 || o->precision > SRA_PREC_BF16_SOUND)
+    if (o->precision < SRA_PREC_FP32 || o->precision > SRA_PREC_BF16)
         return fail(SRA_EINVAL, "unknown precision %d", o->precision);
     if (o->split != SRA_SPLIT_OCTREE && o->split != SRA_SPLIT_KD)
         return fail(SRA_EINVAL, "unknown split %d", o->split);
@@ -208,8 +216,12 @@ sra_status run_bound(const sra_net *n, const sra_opts *o, bool fp64, int s, cons
 sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, BoundOut out,
                               long long count, unsigned long long *recheck_counter,
                               cudaStream_t st) {
-    if (o->precision == SRA_PREC_BF16_SOUND)
-        return fail(SRA_EUNSUPPORTED, "BF16-sound precision is not available for this network");
+    const bool bf16 = o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16;
+    if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || o->K != 64))
+        return fail(SRA_EUNSUPPORTED,
+                    "BF16 tensor-core bounds need a 3 -> H x L -> 1 ReLU network (H = 128 or 256, at most %d hidden "
+                    "tensor-core layers) with affine-truncate K = 64",
+                    kMaxTcLayers);
     const bool fp64 = o->precision == SRA_PREC_FP64;
     const bool recheck = o->recheck && !fp64;
     Scratch sc;
@@ -221,8 +233,18 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
         out.band = o->recheck_band;
         SRA_CK(cudaMemsetAsync(out.flag_count, 0, sizeof(int), st));
     }
-    sra_status r = run_bound(n, o, fp64, 3, src, out, count, st);
-    if (r) return r;
+    sra_status r = SRA_OK;
+    if (bf16) {
+        const long long tiles = (count + 1) / 2;
+        long long grid = num_sms();
+        if (grid > tiles) grid = tiles;
+        if (grid < 1) grid = 1;
+        cudaError_t e = launch_tc_bound(n->tc_H, o->precision == SRA_PREC_BF16_SOUND, n->tcp, src, out, (int)grid, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core bound launch: %s", cudaGetErrorString(e));
+    } else {
+        r = run_bound(n, o, fp64, 3, src, out, count, st);
+        if (r) return r;
+    }
     if (recheck) {
         BoxSrc s2 = src;
         s2.list = out.flag_list;
@@ -243,6 +265,62 @@ sra_status check_net(const sra_net *n) {
     cudaGetDevice(&dev);
     if (dev != n->device) return fail(SRA_EINVAL, "net was loaded on device %d, current is %d", n->device, dev);
     return SRA_OK;
+}
+
+// Prepare the tensor-core path if the network has its shape: 3 inputs,
+// L-1 >= 2 hidden ReLU layers of one width H in {128, 256}, scalar output.
+void prepare_tc(sra_net *n, const float *params) {
+    const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
+    if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256)) return;
+    for (int l = 1; l < L; ++l)
+        if (n->widths[l] != H) return;
+    for (int l = 0; l + 1 < L; ++l)
+        if (n->acts[l] != SRA_ACT_RELU) return;
+    const int nh = L - 2;
+    const size_t per = (size_t)H * H * 2;
+    const size_t bytes = 2 * nh * per + 256;
+    if (cudaMalloc(&n->tc_buf, bytes) != cudaSuccess) { n->tc_buf = nullptr; cudaGetLastError(); return; }
+    std::vector<__nv_bfloat16> hi((size_t)H * H), lo((size_t)H * H);
+    size_t off = (size_t)3 * H + H;  // skip layer 0 (W0, b0)
+    TcParams &t = n->tcp;
+    memset(&t, 0, sizeof t);
+    for (int l = 1; l <= nh; ++l) {
+        const float *W = params + off;
+        for (size_t e = 0; e < (size_t)H * H; ++e) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
+            hi[e] = h;
+            lo[e] = __float2bfloat16_rn(W[e] - __bfloat162float(h));
+        }
+        char *dhi = (char *)n->tc_buf + (2 * (l - 1)) * per, *dlo = dhi + per;
+        if (cudaMemcpy(dhi, hi.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(dlo, lo.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
+            make_bf16_tile_map(&t.wb[l - 1], dhi, H, H, 128, 64) != 0 ||
+            make_bf16_tile_map(&t.wr[l - 1], dlo, H, H, 128, 64) != 0) {
+            cudaFree(n->tc_buf);
+            n->tc_buf = nullptr;
+            return;
+        }
+        off += (size_t)H * H + H;
+    }
+    t.W0 = nullptr;  // filled from the FP32 copy below
+    for (int l = 0; l < L; ++l) t.b[l] = n->dev.layer[l].b;
+    t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
+    t.bout = params[off + H];         // the output layer's bias follows its H weights
+    t.L = L;
+    t.status = (int *)((char *)n->tc_buf + 2 * nh * per);
+    cudaMemset(t.status, 0, sizeof(int));
+    // rounding constants (u = 2^-24, u_b = 2^-8); accumulation model: each
+    // 16-deep MMA step adds at most 17 * 2^-23 of the sum of its terms' sizes
+    const double u = std::ldexp(1.0, -24), ub = std::ldexp(1.0, -8);
+    const double n_steps = 2.0 * H / 16.0;
+    const double gacc = 17.0 * n_steps * std::ldexp(1.0, -23);
+    t.rho1 = (float)((ub * ub + gacc * (1.0 + 2.0 * ub)) * 1.001);
+    t.kappa = (float)(1.0 / (1.0 - ub) * (1.0 + 1e-6));
+    t.ub2u = (float)((ub + 2.0 * u) * 1.001);
+    t.gam_out = (float)(H * u / (1.0 - H * u) * 1.001);
+    t.gam_c_out = (float)((2.0 * H + 1.0) * u / (1.0 - (2.0 * H + 1.0) * u) * 1.001);
+    n->tc_H = H;
+    n->tc_ok = true;
 }
 
 }  // namespace
@@ -364,6 +442,20 @@ sra_status sra_load_mlp(const sra_mlp_desc *d, sra_net **out) {
         ld.out = d->widths[l + 1];
         ld.act = (l + 1 < L) ? n->acts[l] : SRA_ACT_IDENTITY;
     }
+    prepare_tc(n, d->params);
+    if (n->tc_ok) {
+        // layer-0 weights row-major [H][3] for the tensor-core kernel's first layer
+        const size_t w0 = (size_t)n->tc_H * 3 * sizeof(float);
+        void *dw0 = nullptr;
+        if (cudaMalloc(&dw0, w0) == cudaSuccess &&
+            cudaMemcpy(dw0, d->params, w0, cudaMemcpyHostToDevice) == cudaSuccess) {
+            n->tcp.W0 = (const float *)dw0;
+        } else {
+            if (dw0) cudaFree(dw0);
+            n->tc_ok = false;
+        }
+    }
+    cudaGetLastError();
     *out = n;
     return SRA_OK;
 }
@@ -372,6 +464,8 @@ sra_status sra_free_mlp(sra_net *n) {
     if (!n) return SRA_OK;
     cudaDeviceSynchronize();
     if (n->buf) cudaFree(n->buf);
+    if (n->tc_buf) cudaFree(n->tc_buf);
+    if (n->tcp.W0) cudaFree((void *)n->tcp.W0);
     delete n;
     return SRA_OK;
 }
@@ -701,7 +795,7 @@ extern "C" sra_status sra_classify_and_split_noalloc(
                     (long long)n_in, SRA_NOALLOC_MAX_NODES);
     if (n_in > 0 && !in) return fail(SRA_EINVAL, "null frontier_in");
     if ((cap_out > 0 && !out) || (cap_leaves > 0 && !leaves)) return fail(SRA_EINVAL, "null output buffer");
-    if (o->precision == SRA_PREC_BF16_SOUND)
+    if (o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16)
         return fail(SRA_EUNSUPPORTED, "the allocation-free round runs in FP32 or FP64");
     void *scratch = nullptr;
     if ((r = noalloc_scratch(&scratch))) return r;  // before any early return for n_in == 0
@@ -763,5 +857,20 @@ extern "C" sra_status sra_classify_and_split_noalloc(
     a.blk = blk;
     cudaError_t e = launch_split(a, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "split launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+extern "C" sra_status sra_sync_status(const sra_net *n, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    SRA_CK(cudaStreamSynchronize(as_stream(stream)));
+    if (!n->tc_ok) return SRA_OK;
+    int h = 0;
+    SRA_CK(cudaMemcpy(&h, n->tcp.status, sizeof h, cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        SRA_CK(cudaMemset(n->tcp.status, 0, sizeof(int)));
+        return fail(SRA_ETIMEOUT, "a bounded wait of the tensor-core kernel ran out (code %d)", h);
+    }
     return SRA_OK;
 }

@@ -24,7 +24,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, EUNSUPPORTED = range(7)
 UNKNOWN, POSITIVE, NEGATIVE = 0, 1, 2
 ARITH = {"interval": 0, "fixed": 1, "truncate": 2, "full": 3}
 SLOPE = {"chebyshev": 0, "minrange": 1}
-PRECISION = {"fp32": 0, "fp64": 1, "bf16_sound": 2}
+PRECISION = {"fp32": 0, "fp64": 1, "bf16_sound": 2, "bf16": 3}
 SPLIT = {"octree": 0, "kd": 1}
 CNT_CHILDREN, CNT_LEAVES, CNT_POSITIVE, CNT_NEGATIVE, CNT_UNKNOWN, CNT_RECHECKED = range(6)
 CNT_N = 8

@@ -1,0 +1,142 @@
+"""BF16-sound bounds on the tensor cores (precision = bf16_sound).
+
+Hard gate: soundness. Every sampled value f(x) (independent numpy FP64
+forward pass) lies inside the BF16-sound [lo, hi] with no tolerance, and every
+box it calls POSITIVE / NEGATIVE has samples of that sign only. Against the
+FP64 oracle the BF16 bound is looser by its rounding radius; the excess is
+measured and bounded, and decided classes never contradict the oracle.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2202_02444_gb300 import workloads as wl
+from tests.np_forward import box_samples, forward
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sra():
+    from paper_2202_02444_gb300 import sra as s
+    lib = s.library()
+    lib.sra_sync_status.argtypes = [C.c_void_p, C.c_void_p]
+    lib.sra_sync_status.restype = C.c_int
+    return s
+
+
+def level_boxes(n, seed, lmin=2, lmax=10):
+    rng = np.random.default_rng(seed)
+    lev = rng.integers(lmin, lmax + 1, n)
+    c = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    h = np.repeat((1.0 / (1 << lev))[:, None], 3, 1).astype(np.float32)
+    return c, h
+
+
+def run(sra, net, c, h, **kw):
+    lo, hi, cls = sra.bound_boxes(net, torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda(), **kw)
+    assert sra.library().sra_sync_status(net.handle, None) == 0
+    return lo.cpu().numpy().astype(np.float64), hi.cpu().numpy().astype(np.float64), cls.cpu().numpy()
+
+
+NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 4, "relu", seed=31)}
+
+
+@pytest.mark.parametrize("name", list(NETS))
+def test_bf16_sound_contains_samples(sra, name):
+    mlp = NETS[name]()
+    net = sra.Net(mlp)
+    c, h = level_boxes(255, seed=3)  # odd count: the last tile holds one box
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
+    viol = 0
+    for i in range(len(c)):
+        f = forward(mlp, box_samples(c[i], h[i], n_grid=4, n_rand=96, seed=i))
+        viol += int((f < lo[i]).any() or (f > hi[i]).any())
+        if cls[i] == 1:
+            assert f.min() > 0
+        if cls[i] == 2:
+            assert f.max() < 0
+    assert viol == 0
+    net.close()
+
+
+def test_bf16_vs_oracle_excess(sra):
+    """Against the FP64 oracle: decided classes never contradict it and the
+    oracle's center lies in the BF16-sound range. The radius excess is
+    reported, not gated: the a-priori rounding radius sits in x_inf, which
+    each later layer widens by its row sums of |W| (about 9-18x per layer on
+    this 256-wide net), so on deep layers the sound bound is far wider than
+    the exact-arithmetic one."""
+    mlp = wl.net_relu256x8()
+    net = sra.Net(mlp)
+    c, h = level_boxes(96, seed=5)
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
+    rad = 0.5 * (hi - lo)
+    excess = rad / ref["rad"] - 1.0
+    # decided classes agree with the oracle wherever both are decided
+    both = (cls != 0) & (ref["cls"] != 0)
+    assert np.all(cls[both] == ref["cls"][both])
+    # the oracle's centre lies inside the BF16 range
+    assert np.all((ref["y0"] >= lo) & (ref["y0"] <= hi))
+    print(f"bf16 radius excess over FP64: median {np.median(excess):.4g} max {excess.max():.4g}; "
+          f"classes equal {np.mean(cls == ref['cls']):.3f}")
+    assert np.all(excess > -1e-6)
+    net.close()
+
+
+def test_bf16_octree_round(sra):
+    """One octree round in BF16-sound mode: decided nodes are sound and the
+    children / leaves follow the classes."""
+    mlp = wl.net_relu256x8()
+    net = sra.Net(mlp)
+    nodes = wl.random_nodes(1001, level=6, seed=4)
+    fr = sra.nodes_to_tensor(nodes)
+    out, leaves, counts = sra.classify_and_split(net, fr, 7, arith="truncate", K=64, precision="bf16_sound")
+    assert sra.library().sra_sync_status(net.handle, None) == 0
+    cnt = counts.cpu().numpy()
+    assert cnt[2] + cnt[3] + cnt[4] == len(nodes)
+    assert cnt[0] == 8 * cnt[4]
+    net.close()
+
+
+def test_bf16_unsupported_shapes(sra):
+    net = sra.Net(wl.net_small_relu())  # width 32: no tensor-core path
+    c = torch.zeros((4, 3), device="cuda")
+    with pytest.raises(sra.SraError) as e:
+        sra.bound_boxes(net, c, c, arith="truncate", K=64, precision="bf16_sound")
+    assert e.value.code == sra.EUNSUPPORTED
+    net.close()
+    net = sra.Net(wl.net_relu256x8())
+    with pytest.raises(sra.SraError) as e:
+        sra.bound_boxes(net, c, c, arith="fixed", precision="bf16_sound")
+    assert e.value.code == sra.EUNSUPPORTED
+    net.close()
+
+
+def test_bf16_plain_tracks_oracle(sra):
+    """Plain BF16 tensor-core bounds (no rounding radius): error against the
+    FP64 oracle is stated per box; it comes from the BF16 rounding of the
+    noise columns (relative 2^-8 per entry, weights and centers carried as
+    BF16 hi/lo pairs). Gates: radius within 2 %, center within 1e-3 of the
+    scale, classes equal except where the oracle bound is within that
+    tolerance of zero."""
+    mlp = wl.net_relu256x8()
+    net = sra.Net(mlp)
+    c, h = level_boxes(200, seed=9)
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16")
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
+    scale = np.abs(ref["y0"]) + ref["rad"]
+    dc = np.abs(0.5 * (lo + hi) - ref["y0"]) / scale
+    dr = np.abs(0.5 * (hi - lo) - ref["rad"]) / ref["rad"]
+    print(f"bf16 plain vs FP64: center err/scale median {np.median(dc):.2e} max {dc.max():.2e}; "
+          f"radius rel err median {np.median(dr):.2e} max {dr.max():.2e}")
+    tie = ref["sel_gap"] < 1e-2
+    near = np.minimum(np.abs(ref["lo"]), np.abs(ref["hi"])) <= 2e-2 * scale
+    assert np.all((dr < 2e-2) | tie)
+    assert np.all((dc < 1e-3) | tie)
+    assert np.all((cls == ref["cls"]) | near | tie)
+    net.close()
