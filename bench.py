@@ -25,6 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2202_02444_gb300 import workloads as wl  # noqa: E402
+from paper_2202_02444_gb300.shard import weak_shard  # noqa: E402
 
 BOX_FLOP = None  # filled per net (algorithmic FLOP per box-bound eval)
 
@@ -50,6 +51,16 @@ def ray_iter_flops(mlp):
     return f
 
 
+def measured_peak(key, fallback):
+    """A peak from the measured MEASURED_PEAKS.json (else the fallback)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)[key]), "tensor"
+    except (OSError, KeyError, ValueError):
+        return fallback, "tensor"
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,7 +71,7 @@ def parse_args():
     ap.add_argument("--frontier-level", type=int, default=7)
     ap.add_argument("--ray-tile", type=int, default=32, help="ray tile side (tile^2 rays)")
     ap.add_argument("--ray-iters", type=int, default=1500, help="per-ray iteration cap of the ray phase")
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None, choices=["fp32", "bf16_sound", "bf16", "fp64"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
@@ -235,9 +246,11 @@ def main():
     bopts = sra.make_opts(arith="truncate", K=K, precision=args.precision, recheck=True,
                           recheck_band=1e-5)
     # weak scaling: each rank owns its own frontier batch and ray tile
-    fr, n_real = make_frontier(sra, net_box, args.frontier_level, args.batch, bopts)
-    if world > 1:
-        fr = torch.roll(fr, shifts=rank * (fr.shape[0] // max(world, 1)), dims=0).contiguous()
+    # the frontier (a bench input) comes from the FP32 octree of the network
+    fr_all, n_real = make_frontier(sra, net_box, args.frontier_level, args.batch * world,
+                                   sra.make_opts(arith="truncate", K=K))
+    a_, b_ = weak_shard(args.batch, rank)  # this rank's batch of the global frontier
+    fr = fr_all[a_:b_].contiguous()
     B = fr.shape[0]
     o, d = wl.camera_rays(1920, 1080)
     T = args.ray_tile
@@ -271,6 +284,7 @@ def main():
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with ClockSampler(local, enabled=not args.no_clocks) as clk:
+        torch.cuda.nvtx.range_push("timed_steps")  # profilers filter on this range
         for k in range(args.steps):
             flush.zero_()  # evict L2 between steps (outside the events)
             a, b = ev[k]
@@ -278,32 +292,40 @@ def main():
             step_boxes()
             b.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
     box_ms = [a.elapsed_time(b) for a, b in ev]
     cnt = counts.cpu().numpy()
 
-    # the dominant kernel alone: the FP32 bound kernel over the same boxes
+    # the bound kernel alone, in each form, over the same boxes
     nodes_h = sra.tensor_to_nodes(fr)
     w = 2.0 / (1 << nodes_h["level"].astype(np.int64))
     lo_ = -1.0 + np.stack([nodes_h["ix"], nodes_h["iy"], nodes_h["iz"]], 1) * w[:, None]
     cen = torch.from_numpy((lo_ + 0.5 * w[:, None]).astype(np.float32)).to(dev)
     hw = torch.from_numpy(np.repeat((0.5 * w)[:, None], 3, 1).astype(np.float32)).to(dev)
-    kopts = sra.make_opts(arith="truncate", K=K, precision=args.precision)
     blo = torch.empty(B, dtype=torch.float32, device=dev)
     bhi = torch.empty(B, dtype=torch.float32, device=dev)
     bcl = torch.empty(B, dtype=torch.uint8, device=dev)
-    sra.bound_boxes(net_box, cen, hw, opts=kopts, lo=blo, hi=bhi, cls=bcl)
-    kb = []
-    for k in range(3):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
+    forms = {}
+    for prec in ("fp32", "bf16", "bf16_sound"):
+        kopts = sra.make_opts(arith="truncate", K=K, precision=prec)
         sra.bound_boxes(net_box, cen, hw, opts=kopts, lo=blo, hi=bhi, cls=bcl)
-        e1.record()
-        torch.cuda.synchronize()
-        kb.append(e0.elapsed_time(e1))
+        kb = []
+        for k in range(3):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sra.bound_boxes(net_box, cen, hw, opts=kopts, lo=blo, hi=bhi, cls=bcl)
+            e1.record()
+            torch.cuda.synchronize()
+            kb.append(e0.elapsed_time(e1))
+        ms = statistics.median(kb)
+        cl = bcl.cpu().numpy()
+        forms[prec] = {"box_evals_per_s": B / (ms / 1e3), "kernel_ms": ms,
+                       "unknown_frac": float((cl == 0).mean())}
+    kern_ms = forms[args.precision]["kernel_ms"]
 
     # end to end through the public API with host buffers
     fr_host = fr.cpu().pin_memory()
@@ -348,11 +370,17 @@ def main():
     mean_box = float(t_local[0])
     value = world * B / (mean_box / 1e3)
     flop_box = box_flops(mlp_box, K)
-    kern_ms = statistics.median(kb)
     achieved = flop_box * B / (kern_ms / 1e3) / 1e12
     clocks = clk.summary()
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak_fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    if args.precision == "fp32":
+        peak, bound, kname = 152 * 128 * 2 * sm_max * 1e6 / 1e12, "alu", "bound_kernel<float,64> (FP32 FFMA)"
+        peak_src = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
+    else:
+        peak, bound = measured_peak("bf16_tflops", 1900.0)
+        kname = f"tc_bound_kernel<256,{'true' if args.precision == 'bf16_sound' else 'false'}> (tcgen05 BF16)"
+        peak_src = "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS) of measured"
+        bound = "tensor"
     if rank == 0:
         try:
             cpu = cpu_baseline(mlp_box, nodes_h[:max(1, min(B, n_real))], K, args.cpu_sample)
@@ -362,10 +390,11 @@ def main():
             "metric": "box-bound evals/s", "value": value, "unit": "box-bound evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": mean_box, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else args.precision,
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16",
+            "precision": args.precision,
             "data": "synthetic",
             "config": {"workload": f"octree round of ReLU 3-[256]x8-1 (He init, seed 1), "
-                                   f"affine-truncate K={K}, FP64 re-check band 1e-5, "
+                                   f"affine-truncate K={K}, {args.precision}, FP64 re-check band 1e-5, "
                                    f"{B} level-{args.frontier_level} frontier nodes per step",
                        "frontier_nodes": B, "distinct_frontier_nodes": n_real,
                        "l2": "flushed between steps (256 MB write)"},
@@ -375,11 +404,12 @@ def main():
                     "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(statistics.median(d2h_list))},
             "gpu_launches": args.steps * 5,
-            "roofline": {"bound": "alu", "kernel": "bound_kernel<float,64> (FP32 FFMA)",
-                         "achieved": achieved, "peak": peak_fp32, "unit": "TFLOP/s",
-                         "frac": achieved / peak_fp32, "traffic": None,
+            "roofline": {"bound": bound, "kernel": kname,
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
                          "kernel_ms": kern_ms, "flop_per_box": flop_box,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"},
+                         "peak_source": peak_src},
+            "forms": forms,
             "rays": {"workload": f"{T}x{T} central pixels of a 1920x1080 camera at (0,0,3) vs ELU "
                                  f"39(PE 6 octaves)-[512]x6-1, affine-fixed, delta 1e-4, t_max 10, "
                                  f"cap {args.ray_iters} iterations per ray",
