@@ -317,8 +317,10 @@ void prepare_tc(sra_net *n, const float *params) {
     t.rho1 = (float)((ub * ub + gacc * (1.0 + 2.0 * ub)) * 1.001);
     t.kappa = (float)(1.0 / (1.0 - ub) * (1.0 + 1e-6));
     t.ub2u = (float)((ub + 2.0 * u) * 1.001);
-    t.gam_out = (float)(H * u / (1.0 - H * u) * 1.001);
-    t.gam_c_out = (float)((2.0 * H + 1.0) * u / (1.0 - (2.0 * H + 1.0) * u) * 1.001);
+    // output-layer dot products: per part 64 FMAs, then 4 part adds (and the bias)
+    const double nsum = H + 4.0, ncen = 2.0 * H + 5.0;
+    t.gam_out = (float)(nsum * u / (1.0 - nsum * u) * 1.001);
+    t.gam_c_out = (float)(ncen * u / (1.0 - ncen * u) * 1.001);
     n->tc_H = H;
     n->tc_ok = true;
 }
