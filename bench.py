@@ -73,7 +73,8 @@ def parse_args():
     ap.add_argument("--ray-iters", type=int, default=1500, help="per-ray iteration cap of the ray phase")
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
-    ap.add_argument("--kernel-case", default=None, choices=["fp32", "bf16_sound", "bf16", "fp64"],
+    ap.add_argument("--kernel-case", default=None,
+                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="oracle boxes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
@@ -211,6 +212,20 @@ def kernel_case(args):
     3-[256]x8-1 ReLU net, affine-truncate K=64, in the given precision."""
     import torch
     from paper_2202_02444_gb300 import sra
+    if args.kernel_case in ("rays", "rays_bf16"):  # central camera rays, 300-iteration cap
+        net = sra.Net(wl.net_elu512x6_pe())
+        o, d = wl.camera_rays(1920, 1080)
+        side = 8 if args.kernel_case == "rays" else 32
+        sel = np.array([(540 - side // 2 + j) * 1920 + 960 - side // 2 + i
+                        for j in range(side) for i in range(side)])
+        ro, rd = torch.from_numpy(o[sel]).cuda(), torch.from_numpy(d[sel]).cuda()
+        prec = "bf16" if args.kernel_case == "rays_bf16" else "fp32"
+        ropts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=300, precision=prec)
+        for _ in range(2):
+            sra.cast_rays(net, ro, rd, opts=ropts)
+        torch.cuda.synchronize()
+        print("kernel case done rays")
+        return
     net = sra.Net(wl.net_relu256x8())
     c, h = wl.make_boxes(args.batch, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
     C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
@@ -349,19 +364,37 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
         d2h_list.append(cnt_host.numel() * 8 + nch * 8)
 
-    # ray phase (separate from the step): a camera tile with an iteration cap
-    ropts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_iters)
-    sra.cast_rays(net_ray, ro[:64], rd[:64], opts=ropts)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    sra.cast_rays(net_ray, ro, rd, opts=ropts, t_hit=t_hit, iters=iters)
-    e1.record()
-    torch.cuda.synchronize()
-    ray_ms = e0.elapsed_time(e1)
-    iters_h = iters.cpu().numpy()
-    t_h = t_hit.cpu().numpy()
-    done = ~np.isnan(t_h)
+    # ray phase (separate from the step): a camera tile with an iteration cap,
+    # in each form: FP32 on the SIMT cores, split-BF16 hidden layers on tcgen05
+    ray_forms, ray_t = {}, {}
+    it_flop = ray_iter_flops(mlp_ray)
+    for prec in ("fp32", "bf16"):
+        ropts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_iters,
+                              precision=prec)
+        sra.cast_rays(net_ray, ro[:64], rd[:64], opts=ropts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sra.cast_rays(net_ray, ro, rd, opts=ropts, t_hit=t_hit, iters=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        sra.sync_status(net_ray)
+        ray_ms = e0.elapsed_time(e1)
+        iters_h = iters.cpu().numpy()
+        t_h = t_hit.cpu().numpy()
+        done = ~np.isnan(t_h)
+        ray_t[prec] = t_h
+        ray_forms[prec] = {
+            "ms": ray_ms, "rays": R, "completed": int(done.sum()),
+            "rays_per_s": float(done.sum()) / (ray_ms / 1e3),
+            "ray_iters_per_s": float(iters_h.sum()) / (ray_ms / 1e3),
+            "tflops": float(iters_h.sum()) * it_flop / (ray_ms / 1e3) / 1e12,
+            "iters_mean": float(iters_h.mean()), "iters_max": int(iters_h.max()),
+            "hits": int(np.isfinite(t_h).sum())}
+    ta, tb = ray_t["fp32"], ray_t["bf16"]
+    fin = np.isfinite(ta) & np.isfinite(tb)
+    agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
+    agree[fin] &= np.abs(ta[fin] - tb[fin]) <= 1e-4 * 1.0001 + 1e-6
 
     mean_box = statistics.mean(box_ms)
     t_local = torch.tensor([mean_box], dtype=torch.float64, device=dev)
@@ -413,10 +446,10 @@ def main():
             "rays": {"workload": f"{T}x{T} central pixels of a 1920x1080 camera at (0,0,3) vs ELU "
                                  f"39(PE 6 octaves)-[512]x6-1, affine-fixed, delta 1e-4, t_max 10, "
                                  f"cap {args.ray_iters} iterations per ray",
-                     "ms": ray_ms, "rays": R, "completed": int(done.sum()),
-                     "rays_per_s": float(done.sum()) / (ray_ms / 1e3),
-                     "ray_iters_per_s": float(iters_h.sum()) / (ray_ms / 1e3),
-                     "iters_mean": float(iters_h.mean()), "hits": int(np.isfinite(t_h).sum())},
+                     "flop_per_iter": it_flop, "forms": ray_forms,
+                     "same_outcome_frac": float(agree.mean()),
+                     "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
+                     / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
             "cpu_baseline": cpu,
             "clocks": clocks,
             "wall_s": wall,

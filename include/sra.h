@@ -186,6 +186,15 @@ sra_status sra_classify_and_split(const sra_net *net, const sra_opts *opts,
  * t_hit[i] (device float[n]): the returned t on a hit, +inf for NO_HIT, NaN
  * when opts->max_iters ran out; and iters[i] (device int32[n], may be NULL):
  * loop iterations taken. One persistent launch refills finished ray slots.
+ * opts->precision: SRA_PREC_FP32 runs every step on the SIMT cores in FP32
+ * (any arithmetic); SRA_PREC_BF16 runs the hidden H -> H layers on the tensor
+ * cores (tcgen05) with the weights and every operand split into BF16 hi/lo
+ * pairs and FP32 accumulation (about 16 significant bits per product; plain
+ * arithmetic, no rounding radius). BF16 needs affine-fixed arithmetic and a
+ * network whose hidden layers all have one width H in {128, 256, 512}, with
+ * 1 to 8 H -> H layers and an input width (after the encoding) of at most 64;
+ * otherwise SRA_EUNSUPPORTED. A bounded wait of that kernel that runs out is
+ * reported by sra_sync_status as SRA_ETIMEOUT.
  * Errors: SRA_EINVAL (delta <= 0, bad steps), SRA_EUNSUPPORTED, SRA_ECUDA.
  * Asynchronous. */
 sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *origins,

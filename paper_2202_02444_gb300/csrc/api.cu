@@ -13,6 +13,7 @@
 #include "launch.h"
 #include "tc_bound.h"
 #include "tc_host.h"
+#include "tc_rays.h"
 
 using namespace sra;
 
@@ -30,6 +31,11 @@ struct sra_net {
     int tc_H = 0;
     void *tc_buf = nullptr;  // bf16 hi/lo weights of the hidden layers, status word
     TcParams tcp;
+    // tensor-core ray kernel (din -> H x (L-1) -> 1 nets, H = 128/256/512)
+    bool tcr_ok = false;
+    int tcr_H = 0;
+    void *tcr_buf = nullptr;  // W_b, W_r, |W_b|, sign(W_b) W_r per hidden layer, status word
+    TcRayParams tcrp;
 };
 
 namespace {
@@ -325,6 +331,63 @@ void prepare_tc(sra_net *n, const float *params) {
     n->tc_ok = true;
 }
 
+// Prepare the tensor-core ray kernel if the network has its shape: every
+// hidden width H in {128, 256, 512}, 1 <= L-2 <= 8 hidden H -> H layers, an
+// input width (after the positional encoding) of at most 64, scalar output.
+void prepare_tc_rays(sra_net *n, const float *params) {
+    const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
+    if (L < 3 || L - 2 > kMaxRayTc || (H != 128 && H != 256 && H != 512)) return;
+    if (n->din > tc_ray_max_din()) return;
+    for (int l = 1; l < L; ++l)
+        if (n->widths[l] != H) return;
+    const int nh = L - 2;
+    const size_t per = (size_t)H * H * 2;
+    const size_t bytes = 4 * nh * per + 256;
+    if (cudaMalloc(&n->tcr_buf, bytes) != cudaSuccess) { n->tcr_buf = nullptr; cudaGetLastError(); return; }
+    std::vector<__nv_bfloat16> mats(4 * (size_t)H * H);
+    size_t off = (size_t)n->din * H + H;  // skip layer 0 (W0, b0)
+    TcRayParams &t = n->tcrp;
+    memset(&t, 0, sizeof t);
+    for (int l = 1; l <= nh; ++l) {
+        const float *W = params + off;
+        __nv_bfloat16 *wb = mats.data(), *wr = wb + (size_t)H * H, *wa = wr + (size_t)H * H,
+                      *ws = wa + (size_t)H * H;
+        for (size_t e = 0; e < (size_t)H * H; ++e) {
+            const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
+            const float hf = __bfloat162float(h);
+            const __nv_bfloat16 r = __float2bfloat16_rn(W[e] - hf);
+            wb[e] = h;
+            wr[e] = r;
+            wa[e] = __float2bfloat16_rn(std::fabs(hf));
+            ws[e] = __float2bfloat16_rn(hf < 0.f ? -__bfloat162float(r) : __bfloat162float(r));
+        }
+        char *d = (char *)n->tcr_buf + 4 * (l - 1) * per;
+        if (cudaMemcpy(d, mats.data(), 4 * per, cudaMemcpyHostToDevice) != cudaSuccess ||
+            make_bf16_tile_map(&t.wb[l - 1], d, H, H, 128, 64) != 0 ||
+            make_bf16_tile_map(&t.wr[l - 1], d + per, H, H, 128, 64) != 0 ||
+            make_bf16_tile_map(&t.wa[l - 1], d + 2 * per, H, H, 128, 64) != 0 ||
+            make_bf16_tile_map(&t.ws[l - 1], d + 3 * per, H, H, 128, 64) != 0) {
+            cudaFree(n->tcr_buf);
+            n->tcr_buf = nullptr;
+            cudaGetLastError();
+            return;
+        }
+        off += (size_t)H * H + H;
+    }
+    t.W0t = n->dev.layer[0].Wt;  // [din][H]
+    for (int l = 0; l < L; ++l) t.b[l] = n->dev.layer[l].b;
+    for (int l = 0; l + 1 < L; ++l) t.act[l] = n->acts[l];
+    t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
+    t.bout = params[off + H];
+    t.L = L;
+    t.din = n->din;
+    t.pe = n->pe;
+    t.status = (int *)((char *)n->tcr_buf + 4 * nh * per);
+    cudaMemset(t.status, 0, sizeof(int));
+    n->tcr_H = H;
+    n->tcr_ok = true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -445,6 +508,7 @@ sra_status sra_load_mlp(const sra_mlp_desc *d, sra_net **out) {
         ld.act = (l + 1 < L) ? n->acts[l] : SRA_ACT_IDENTITY;
     }
     prepare_tc(n, d->params);
+    prepare_tc_rays(n, d->params);
     if (n->tc_ok) {
         // layer-0 weights row-major [H][3] for the tensor-core kernel's first layer
         const size_t w0 = (size_t)n->tc_H * 3 * sizeof(float);
@@ -468,6 +532,7 @@ sra_status sra_free_mlp(sra_net *n) {
     if (n->buf) cudaFree(n->buf);
     if (n->tc_buf) cudaFree(n->tc_buf);
     if (n->tcp.W0) cudaFree((void *)n->tcp.W0);
+    if (n->tcr_buf) cudaFree(n->tcr_buf);
     delete n;
     return SRA_OK;
 }
@@ -597,8 +662,13 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
         o->max_iters < 1)
         return fail(SRA_EINVAL, "ray options out of range (delta, t_max, sigma0 > 0; eta+ >= 1; "
                                 "0 < eta- < 1; 0 < safety <= 1; max_iters >= 1)");
-    if (o->precision != SRA_PREC_FP32)
-        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32");
+    const bool tc = o->precision == SRA_PREC_BF16;
+    if (o->precision != SRA_PREC_FP32 && !tc)
+        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32 or (tensor cores) BF16");
+    if (tc && (!n->tcr_ok || o->arith != SRA_ARITH_AFFINE_FIXED))
+        return fail(SRA_EUNSUPPORTED, "BF16 cast_rays needs affine-fixed arithmetic and a net of "
+                                      "uniform hidden width 128/256/512 with 1..%d hidden layers and "
+                                      "input width <= %d", kMaxRayTc, tc_ray_max_din());
     cudaStream_t st = as_stream(stream);
     Scratch sc;
     const size_t f0_bytes = align16((size_t)count * 4);
@@ -608,6 +678,30 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
     // f(p) at every origin: the reference sign of DifferentSigns (Proc. 2)
     if ((r = sra_eval(n, origins, count, f0, stream))) return r;
     SRA_CK(cudaMemsetAsync(next, 0, 8, st));
+    if (tc) {
+        TcRayParams p = n->tcrp;
+        p.slope = o->slope;
+        p.origins = origins;
+        p.dirs = dirs;
+        p.f0 = f0;
+        p.t_hit = t_hit;
+        p.iters = iters;
+        p.n = count;
+        p.next = next;
+        p.delta = o->delta;
+        p.t_max = o->t_max;
+        p.sigma0 = o->sigma0;
+        p.eta_plus = o->eta_plus;
+        p.eta_minus = o->eta_minus;
+        p.safety = o->safety;
+        p.max_iters = o->max_iters;
+        long long grid = num_sms();
+        const long long need = (count + 7) / 8;
+        if (grid > need) grid = need;
+        cudaError_t e = launch_tc_rays(n->tcr_H, p, (int)grid, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core ray kernel launch: %s", cudaGetErrorString(e));
+        return SRA_OK;
+    }
     int kmax = 0;
     if ((r = kmax_for(n, o, 1, &kmax))) return r;
     RangeCfg cfg;
@@ -867,12 +961,15 @@ extern "C" sra_status sra_sync_status(const sra_net *n, void *stream) {
     sra_status r = check_net(n);
     if (r) return r;
     SRA_CK(cudaStreamSynchronize(as_stream(stream)));
-    if (!n->tc_ok) return SRA_OK;
-    int h = 0;
-    SRA_CK(cudaMemcpy(&h, n->tcp.status, sizeof h, cudaMemcpyDeviceToHost));
-    if (h != 0) {
-        SRA_CK(cudaMemset(n->tcp.status, 0, sizeof(int)));
-        return fail(SRA_ETIMEOUT, "a bounded wait of the tensor-core kernel ran out (code %d)", h);
+    int *words[2] = {n->tc_ok ? n->tcp.status : nullptr, n->tcr_ok ? n->tcrp.status : nullptr};
+    for (int *w : words) {
+        if (!w) continue;
+        int h = 0;
+        SRA_CK(cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost));
+        if (h != 0) {
+            SRA_CK(cudaMemset(w, 0, sizeof(int)));
+            return fail(SRA_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (code %d)", h);
+        }
     }
     return SRA_OK;
 }

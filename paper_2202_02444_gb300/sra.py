@@ -66,8 +66,9 @@ _lib.sra_extract_leaves.argtypes = [_vp, C.POINTER(Opts), C.POINTER(C.c_float),
                                     C.POINTER(C.c_float), C.c_int32, _vp, C.c_int64,
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]
 _lib.sra_eval.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
+_lib.sra_sync_status.argtypes = [_vp, _vp]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
-           "sra_cast_rays", "sra_extract_leaves", "sra_eval"):
+           "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -110,6 +111,12 @@ def _stream():
 
 def _ptr(t):
     return _vp(t.data_ptr()) if t is not None else _vp(0)
+
+
+def sync_status(net):
+    """Synchronise the current stream and raise if a tensor-core kernel of
+    this net reported a bounded wait that ran out (sra_sync_status)."""
+    _check(_lib.sra_sync_status(net.handle, _stream()))
 
 
 def _need(t, dtype, shape_last=None, name="tensor"):

@@ -34,7 +34,8 @@ def check(t, ref, delta, margin_band, max_frac=0.02):
     at most max_frac of the rays may."""
     hit_g, hit_r = np.isfinite(t), ref["status"] == 1
     cap_g, cap_r = np.isnan(t), ref["status"] == 2
-    far = hit_g & hit_r & (np.abs(t - ref["t"]) > delta * 1.0001 + 1e-6)
+    with np.errstate(invalid="ignore"):  # inf - inf on misses, masked out below
+        far = hit_g & hit_r & (np.abs(t - ref["t"]) > delta * 1.0001 + 1e-6)
     mism = (hit_g != hit_r) | (cap_g != cap_r) | far
     unexplained = mism & (ref["margin"] >= margin_band)
     assert not unexplained.any(), np.nonzero(unexplained)[0][:10]
