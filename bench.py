@@ -76,6 +76,9 @@ def parse_args():
     ap.add_argument("--kernel-case", default=None,
                     choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
+    ap.add_argument("--serve-rates", default="2,8", help="request rates (req/s) of the serving sweep")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="oracle boxes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
     return ap.parse_args()
@@ -138,6 +141,101 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def serving_nets():
+    """16 resident networks: twelve of the uneven multi-network generator and
+    four 39(PE)-[512]x6-1 ELU networks (seeds 2..5)."""
+    return [wl.net_batch_mix(i) for i in range(12)] + \
+        [wl.make_mlp([512] * 6, "elu", seed=2 + k, pe_octaves=6, name=f"elu_pe6_512x6_s{2 + k}")
+         for k in range(4)]
+
+
+def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
+    """Poisson request traces (seed 5) against 16 resident networks through
+    sra_serve: a third each of 64x64 ray tiles (cap 200 iterations per ray),
+    batches of U[256, 65536] boxes and leaf-extraction jobs to depth 9 (frontier
+    capacity 2^20 nodes per level). Each request takes the BF16 form (tensor
+    cores) with probability 1/2 where its network has that kernel, else FP32.
+    Returns p50 / p99 latency (arrival to completion) and throughput per rate."""
+    mlps = serving_nets()
+    nets = [sra.Net(m) for m in mlps]
+    forms = [sra.make_opts(arith="fixed", delta=1e-3, max_iters=200),                     # rays FP32
+             sra.make_opts(arith="truncate", K=16),                                       # boxes / leaves FP32
+             sra.make_opts(arith="fixed", delta=1e-3, max_iters=200, precision="bf16"),   # rays BF16
+             sra.make_opts(arith="truncate", K=64, precision="bf16_sound", recheck=True)]  # boxes BF16-sound
+
+    def uniform(m, H):
+        return all(w == H for w in m.widths[1:-1]) and 1 <= m.n_layers - 2 <= 8
+
+    ray_tc = [any(uniform(m, H) for H in (128, 256, 512)) and m.widths[0] <= 64 for m in mlps]
+    box_tc = [any(uniform(m, H) for H in (128, 256)) and all(a == 1 for a in m.acts) and
+              m.pe_octaves == 0 and m.n_layers - 2 <= 12 for m in mlps]
+    o_all, d_all = wl.camera_rays(64, 64)
+    ro, rd = torch.from_numpy(o_all).to(dev), torch.from_numpy(d_all).to(dev)
+    out = {"workload": "16 resident nets (12 of the uneven generator, seeds 1000..1011, + 4 ELU "
+                       "39(PE)-[512]x6-1, seeds 2..5); Poisson arrivals (seed 5); 1/3 each: 64x64 "
+                       "camera ray tile (affine-fixed, delta 1e-3, cap 200 iterations), U[256,65536] "
+                       "boxes (affine-truncate K=16 FP32 / K=64 BF16-sound), leaf extraction to depth 9 "
+                       "(K=16, frontier cap 2^20 per level); BF16 form for half the requests whose net "
+                       "has that kernel",
+           "slots": slots, "frontier_budget_bytes": budget, "rates": []}
+    for lam in rates:
+        rng = np.random.default_rng(5)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_req))
+        reqs, keep, meta = [], [], []
+        for i in range(n_req):
+            kind = int(rng.integers(0, 3))
+            j = int(rng.integers(0, len(mlps)))
+            bf = bool(rng.random() < 0.5)
+            if kind == 0:
+                form = 2 if (bf and ray_tc[j]) else 0
+                t = torch.empty(ro.shape[0], dtype=torch.float32, device=dev)
+                it = torch.empty(ro.shape[0], dtype=torch.int32, device=dev)
+                keep.append((t, it))
+                reqs.append(sra.ray_request(j, form, arrivals[i], ro, rd, t, it))
+            elif kind == 1:
+                n = int(rng.integers(256, 65537))
+                c, h = wl.make_boxes(n, seed=300 + i)
+                c, h = torch.from_numpy(c).to(dev), torch.from_numpy(h).to(dev)
+                lo = torch.empty(n, dtype=torch.float32, device=dev)
+                hi = torch.empty(n, dtype=torch.float32, device=dev)
+                cl = torch.empty(n, dtype=torch.uint8, device=dev)
+                keep.append((c, h, lo, hi, cl))
+                form = 3 if (bf and box_tc[j]) else 1
+                reqs.append(sra.box_request(j, form, arrivals[i], c, h, lo, hi, cl))
+            else:
+                leaves = torch.empty((1 << 20, 4), dtype=torch.int16, device=dev)
+                keep.append(leaves)
+                form = 1
+                reqs.append(sra.leaf_request(j, form, arrivals[i], 9, leaves))
+            meta.append((kind, form))
+        torch.cuda.synchronize()
+        res = sra.serve(nets, forms, reqs, slots=slots, frontier_bytes=budget, realtime=True)
+        lat = np.array([r.t_done - r.arrival for r in res]) * 1e3
+        span = max(r.t_done for r in res) - min(r.arrival for r in res)
+        st = np.array([r.status for r in res])
+        per = {}
+        for name, sel in (("rays", [m[0] == 0 for m in meta]), ("boxes", [m[0] == 1 for m in meta]),
+                          ("leaves", [m[0] == 2 for m in meta]),
+                          ("bf16_form", [m[1] in (2, 3) for m in meta]),
+                          ("fp32_form", [m[1] in (0, 1) for m in meta])):
+            sel = np.array(sel)
+            if sel.any():
+                per[name] = {"n": int(sel.sum()), "p50_ms": float(np.percentile(lat[sel], 50)),
+                             "p99_ms": float(np.percentile(lat[sel], 99))}
+        out["rates"].append({
+            "offered_req_per_s": lam, "requests": n_req,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "throughput_req_per_s": n_req / span,
+            "ok": int((st == 0).sum()), "capacity_exceeded": int((st == 5).sum()),
+            "other_errors": int(((st != 0) & (st != 5)).sum()),
+            "max_concurrent_slots_used": len({r.slot for r in res if r.slot >= 0}),
+            "by": per})
+        del keep
+    for n in nets:
+        n.close()
+    return out
 
 
 def make_frontier(sra, net, level, batch, opts):
@@ -396,6 +494,11 @@ def main():
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
     agree[fin] &= np.abs(ta[fin] - tb[fin]) <= 1e-4 * 1.0001 + 1e-6
 
+    serving = None
+    if not args.no_serve and rank == 0:
+        rates = [float(x) for x in args.serve_rates.split(",") if x]
+        serving = serving_phase(sra, torch, dev, rates, args.serve_requests)
+
     mean_box = statistics.mean(box_ms)
     t_local = torch.tensor([mean_box], dtype=torch.float64, device=dev)
     if world > 1:
@@ -450,6 +553,7 @@ def main():
                      "same_outcome_frac": float(agree.mean()),
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
                      / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "wall_s": wall,

@@ -258,6 +258,70 @@ sra_status sra_selftest_tc_gemm(const void *W, const void *X, float *D, int *sta
  * their outputs are undefined). The record is cleared. */
 sra_status sra_sync_status(const sra_net *net, void *stream);
 
+/* ---- Serving: continuous batching over resident networks ----------------
+ * Not a procedure of the paper: a request loop around Proc. 1-3 for many
+ * concurrent queries. sra_serve runs a whole request trace. Requests become
+ * eligible at their arrival time; the loop admits them first come, first
+ * served, each into a free slot (one CUDA stream per slot) when the device
+ * memory it reserves fits in the frontier budget, and drives every admitted
+ * request on its slot's stream while others run, so the work of several
+ * requests overlaps on the device. A leaf job is stepped one octree level at
+ * a time (Proc. 3); between its levels the loop serves other slots.
+ *
+ * Memory: the loop allocates one device arena of cfg->frontier_bytes and
+ * one stream per slot when it starts and frees them before it returns. A
+ * leaf job takes its two frontier buffers (2 * cap * sizeof(sra_node)) and
+ * its counters from the arena; ray and box requests reserve their
+ * stream-ordered scratch size (16 bytes per ray / box) from the same budget.
+ * A request whose reservation exceeds the whole budget ends at once with
+ * SRA_ENOMEM.
+ *
+ * Results are the same as a lone call of the entry point each kind uses
+ * (sra_cast_rays, sra_bound_boxes, sra_classify_and_split level by level).
+ */
+enum { SRA_REQ_RAYS = 0, SRA_REQ_BOXES = 1, SRA_REQ_LEAVES = 2 };
+
+typedef struct {
+    int32_t kind;          /* SRA_REQ_* */
+    int32_t net;           /* index into nets[] */
+    int32_t form;          /* index into forms[] (the sra_opts of this request) */
+    int32_t depth;         /* LEAVES: octree depth (root box [-1,1]^3 is level 0) */
+    double arrival;        /* seconds after the trace starts; non-decreasing */
+    int64_t n;             /* RAYS: rays; BOXES: boxes */
+    const float *a, *b;    /* RAYS: origins, dirs; BOXES: centers, half-widths
+                              (device float[n][3]) */
+    float *lo, *hi;        /* RAYS: lo = t_hit (device float[n]), hi unused;
+                              BOXES: range bounds (device float[n]) */
+    int32_t *iters;        /* RAYS: iterations per ray (device int32[n]; may be NULL) */
+    uint8_t *cls;          /* BOXES: classes (device uint8[n]; may be NULL) */
+    sra_node *leaves;      /* LEAVES: UNKNOWN nodes at `depth` (device sra_node[cap]) */
+    int64_t cap;           /* LEAVES: capacity of leaves and of each frontier level */
+    /* written by sra_serve */
+    int64_t n_out;         /* LEAVES: leaves found (or children needed on overflow) */
+    int32_t status;        /* sra_status of this request */
+    int32_t slot;          /* slot that ran it (-1: never admitted) */
+    int32_t levels;        /* LEAVES: levels completed */
+    int32_t pad;
+    double t_admit, t_done;/* seconds after the trace starts */
+} sra_request;
+
+typedef struct {
+    int32_t slots;          /* concurrent requests, 1..64 */
+    int32_t realtime;       /* 1: a request is eligible at its arrival time;
+                               0: every request is eligible at once */
+    int64_t frontier_bytes; /* device memory budget of admitted requests */
+} sra_serve_cfg;
+
+/* Runs the trace reqs[0..n_req) against nets[0..n_nets) (all loaded on the
+ * current device) with the option sets forms[0..n_forms). Returns SRA_OK
+ * when every request has ended (each request's own outcome is in its
+ * `status`); SRA_EINVAL for bad arguments (a net or form index out of range,
+ * arrivals out of order); SRA_ENOMEM / SRA_ECUDA if the arena, a stream or a
+ * CUDA call of the loop itself fails. Synchronous: returns after all device
+ * work of the trace has finished. */
+sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, const sra_opts *forms,
+                     int32_t n_forms, const sra_serve_cfg *cfg, sra_request *reqs, int64_t n_req);
+
 /* Description of the last error on this thread ("" if none). */
 const char *sra_last_error(void);
 

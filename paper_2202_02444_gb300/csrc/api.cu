@@ -390,6 +390,16 @@ void prepare_tc_rays(sra_net *n, const float *params) {
 
 }  // namespace
 
+sra_status sra::set_error(sra_status s, const char *fmt, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(b, sizeof b, fmt, ap);
+    va_end(ap);
+    g_err = b;
+    return s;
+}
+
 extern "C" {
 
 const char *sra_last_error(void) { return g_err.c_str(); }

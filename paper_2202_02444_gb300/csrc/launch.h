@@ -7,6 +7,9 @@
 
 namespace sra {
 
+// Record an error message for sra_last_error() and return s.
+sra_status set_error(sra_status s, const char *fmt, ...);
+
 __host__ __device__ constexpr int engine_row_stride(int kmax) { return ((kmax + 3 + 3) / 4) * 4; }
 
 // KMAX values the engine is instantiated for.

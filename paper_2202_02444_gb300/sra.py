@@ -52,6 +52,23 @@ class Opts(C.Structure):
                 ("safety", C.c_float), ("max_iters", C.c_int64)]
 
 
+class Request(C.Structure):
+    """One query of a serving trace (sra_request)."""
+    _fields_ = [("kind", C.c_int32), ("net", C.c_int32), ("form", C.c_int32), ("depth", C.c_int32),
+                ("arrival", C.c_double), ("n", C.c_int64),
+                ("a", C.c_void_p), ("b", C.c_void_p), ("lo", C.c_void_p), ("hi", C.c_void_p),
+                ("iters", C.c_void_p), ("cls", C.c_void_p), ("leaves", C.c_void_p),
+                ("cap", C.c_int64), ("n_out", C.c_int64), ("status", C.c_int32),
+                ("slot", C.c_int32), ("levels", C.c_int32), ("pad", C.c_int32),
+                ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class ServeCfg(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("realtime", C.c_int32), ("frontier_bytes", C.c_int64)]
+
+
+REQ_RAYS, REQ_BOXES, REQ_LEAVES = 0, 1, 2
+
 _vp = C.c_void_p
 _lib.sra_last_error.restype = C.c_char_p
 _lib.sra_default_opts.argtypes = [C.POINTER(Opts)]
@@ -67,8 +84,10 @@ _lib.sra_extract_leaves.argtypes = [_vp, C.POINTER(Opts), C.POINTER(C.c_float),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]
 _lib.sra_eval.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
 _lib.sra_sync_status.argtypes = [_vp, _vp]
+_lib.sra_serve.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(Opts), C.c_int32,
+                           C.POINTER(ServeCfg), C.POINTER(Request), C.c_int64]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
-           "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status"):
+           "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -249,3 +268,40 @@ def extract_leaves(net, depth, xl=(-1.0, -1.0, -1.0), xu=(1.0, 1.0, 1.0), opts=N
     _check(code)
     counts = np.array(list(lc), np.int64).reshape(depth + 1, 3)
     return leaves[:nl.value], counts
+
+
+def ray_request(net, form, arrival, origins, dirs, t_hit, iters=None):
+    """A ray-tile query (Proc. 2) for serve(); the tensors must stay alive."""
+    for t, nm in ((origins, "origins"), (dirs, "dirs")):
+        _need(t, torch.float32, 3, nm)
+    _need(t_hit, torch.float32, None, "t_hit")
+    return Request(kind=REQ_RAYS, net=net, form=form, arrival=float(arrival), n=origins.shape[0],
+                   a=_ptr(origins), b=_ptr(dirs), lo=_ptr(t_hit), iters=_ptr(iters))
+
+
+def box_request(net, form, arrival, centers, halfw, lo, hi, cls=None):
+    """A box-batch query (Proc. 1) for serve(); the tensors must stay alive."""
+    _need(centers, torch.float32, 3, "centers")
+    _need(halfw, torch.float32, 3, "halfw")
+    return Request(kind=REQ_BOXES, net=net, form=form, arrival=float(arrival), n=centers.shape[0],
+                   a=_ptr(centers), b=_ptr(halfw), lo=_ptr(lo), hi=_ptr(hi), cls=_ptr(cls))
+
+
+def leaf_request(net, form, arrival, depth, leaves):
+    """A leaf-extraction job (Proc. 3 to `depth`) for serve(); leaves is a
+    CUDA int16 [cap, 4] tensor that also sets the frontier capacity."""
+    return Request(kind=REQ_LEAVES, net=net, form=form, arrival=float(arrival), depth=int(depth),
+                   leaves=_ptr(leaves), cap=leaves.shape[0])
+
+
+def serve(nets, forms, requests, slots=4, frontier_bytes=256 << 20, realtime=True):
+    """Run a request trace through sra_serve on the current device; the
+    Request objects are filled in place (status, slot, t_admit, t_done,
+    n_out, levels) and returned as a ctypes array."""
+    torch.cuda.synchronize()
+    arr = (Request * max(1, len(requests)))(*requests)
+    handles = (_vp * len(nets))(*[n.handle for n in nets])
+    fo = (Opts * len(forms))(*forms)
+    cfg = ServeCfg(int(slots), int(bool(realtime)), int(frontier_bytes))
+    _check(_lib.sra_serve(handles, len(nets), fo, len(forms), C.byref(cfg), arr, len(requests)))
+    return arr[:len(requests)]
