@@ -113,6 +113,12 @@ typedef struct {
     float eta_minus;     /* step shrink on failure (0.5) */
     float safety;        /* step fraction taken (App. B: 0.98) */
     int64_t max_iters;   /* per-ray iteration cap; the ray then reports NaN */
+    int32_t block_threads; /* SIMT bound kernels: threads per CTA (boxes per CTA
+                              = block_threads / padded width); 0 = 256. A
+                              multiple of 32 in [32, 1024], capped by what the
+                              noise-column count allows (the tile shape the
+                              autotuner chooses) */
+    int32_t reserved;
 } sra_opts;
 
 /* Octree / k-d node: integer cell coordinates at `level` inside the root box
@@ -180,6 +186,37 @@ sra_status sra_classify_and_split(const sra_net *net, const sra_opts *opts,
                                   sra_node *frontier_out, int64_t cap_out,
                                   sra_node *leaves_out, int64_t cap_leaves,
                                   int64_t *counts, void *stream);
+
+/* One segment of a batched round (sra_classify_and_split_batch): the
+ * frontier of one network. */
+typedef struct {
+    int32_t net;          /* index into nets[] and opts[] */
+    int32_t max_level;    /* octree (k-d) depth of this network's tree */
+    int64_t first, n;     /* its nodes: frontier_in[first, first + n) */
+    int64_t out_first;    /* children go to frontier_out[out_first, out_first + cap_out) */
+    int64_t cap_out;
+    int64_t leaf_first;   /* UNKNOWN nodes at max_level go to leaves_out[leaf_first, + cap_leaves) */
+    int64_t cap_leaves;
+} sra_batch_seg;
+
+/* One round of Proc. 3 over the frontiers of many networks at once: the
+ * batched form of sra_classify_and_split for uneven workloads. Every
+ * segment's results (classes, children, leaves, counters) equal those of a
+ * lone sra_classify_and_split call on that segment (root box [root_lo,
+ * root_hi] for all). The bounds of all segments whose option sets need the
+ * same noise-column bound run in one persistent launch (a chunk queue that
+ * hands each CTA groups of nodes of one network, heaviest networks first),
+ * and one segmented compaction serves every segment. counts: device
+ * int64[n_segs][SRA_CNT_N], zeroed by the caller (or holding earlier
+ * chunks' totals, which are appended after). FP32 only: every opts[k] has
+ * precision SRA_PREC_FP32 and recheck 0, else SRA_EUNSUPPORTED. Segments
+ * must not overlap in frontier_out or leaves_out. Uses stream-ordered scratch
+ * of about 2 KB per segment plus one byte per node. Asynchronous. */
+sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_opts *opts,
+                                        int32_t n_nets, const float *root_lo, const float *root_hi,
+                                        const sra_node *frontier_in, const sra_batch_seg *segs,
+                                        int32_t n_segs, sra_node *frontier_out, sra_node *leaves_out,
+                                        int64_t *counts, void *stream);
 
 /* Proc. 2 (CastRay) for n rays p = origins[i], r = dirs[i] (device
  * float[n][3]; r need not be unit length; t is in units of r). Writes

@@ -2,6 +2,7 @@
 // shared-memory layout, stream-ordered scratch and the level loop of the
 // fixed-depth tree build (Proc. 3). Every step of the path runs in the
 // kernels of this library.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cmath>
@@ -133,6 +134,8 @@ sra_status check_opts(const sra_opts *o) {
         return fail(SRA_EINVAL, "unknown precision %d", o->precision);
     if (o->split != SRA_SPLIT_OCTREE && o->split != SRA_SPLIT_KD)
         return fail(SRA_EINVAL, "unknown split %d", o->split);
+    if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > 1024 || o->block_threads % 32))
+        return fail(SRA_EINVAL, "block_threads %d: 0 or a multiple of 32 in [32, 1024]", o->block_threads);
     if (!(o->recheck_band >= 0.f)) return fail(SRA_EINVAL, "recheck_band must be >= 0");
     return SRA_OK;
 }
@@ -205,7 +208,7 @@ sra_status run_bound(const sra_net *n, const sra_opts *o, bool fp64, int s, cons
     sra_status r = kmax_for(n, o, s, &kmax);
     if (r) return r;
     RangeCfg cfg;
-    r = make_cfg(n, o, kmax, fp64 ? 8 : 4, 256, &cfg);
+    r = make_cfg(n, o, kmax, fp64 ? 8 : 4, o->block_threads > 0 ? o->block_threads : 256, &cfg);
     if (r) return r;
     long long groups = (n_hint + cfg.NB - 1) / cfg.NB;
     long long cap = (long long)num_sms() * 64;
@@ -654,6 +657,133 @@ sra_status sra_classify_and_split(const sra_net *n, const sra_opts *o, const flo
     a.blk = blk;
     cudaError_t e = launch_split(a, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "split launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_opts *opts, int32_t n_nets,
+                                        const float *root_lo, const float *root_hi, const sra_node *in,
+                                        const sra_batch_seg *segs, int32_t n_segs, sra_node *out,
+                                        sra_node *leaves, int64_t *counts, void *stream) {
+    g_err.clear();
+    if (!nets || !opts || n_nets < 1 || !segs || n_segs < 1 || !root_lo || !root_hi || !counts)
+        return fail(SRA_EINVAL, "null or empty nets / opts / segs / root / counts");
+    for (int d = 0; d < 3; ++d)
+        if (!(root_hi[d] > root_lo[d])) return fail(SRA_EINVAL, "empty root box on axis %d", d);
+    sra_status r;
+    for (int k = 0; k < n_nets; ++k) {
+        if ((r = check_net(nets[k]))) return r;
+        if ((r = check_opts(&opts[k]))) return r;
+        if (opts[k].precision != SRA_PREC_FP32 || opts[k].recheck)
+            return fail(SRA_EUNSUPPORTED, "batched rounds run in FP32 without re-check (opts[%d])", k);
+    }
+    cudaStream_t st = as_stream(stream);
+    unsigned char n3[kMaxKdLevels][3], axis[kMaxKdLevels];
+    kd_tables(root_lo, root_hi, n3, axis);
+    std::vector<BatchSegDev> ds(n_segs);
+    std::vector<BatchSplitSeg> ss(n_segs);
+    std::vector<int> kmaxes(n_segs);
+    std::vector<double> chunk_cost(n_segs);
+    long long cls_n = 0, nblk = 0;
+    for (int s = 0; s < n_segs; ++s) {
+        const sra_batch_seg &g = segs[s];
+        if (g.net < 0 || g.net >= n_nets) return fail(SRA_EINVAL, "segment %d: net %d out of range", s, g.net);
+        const sra_net *n = nets[g.net];
+        const sra_opts *o = &opts[g.net];
+        const int lvl_cap = (o->split == SRA_SPLIT_OCTREE) ? 16 : kMaxKdLevels - 1;
+        if (g.max_level < 0 || g.max_level > lvl_cap)
+            return fail(SRA_EINVAL, "segment %d: max_level %d outside [0, %d]", s, g.max_level, lvl_cap);
+        if (g.first < 0 || g.n < 0 || g.n > INT32_MAX || g.out_first < 0 || g.cap_out < 0 || g.leaf_first < 0 ||
+            g.cap_leaves < 0)
+            return fail(SRA_EINVAL, "segment %d: negative or oversized range", s);
+        if ((g.n > 0 && !in) || (g.cap_out > 0 && !out) || (g.cap_leaves > 0 && !leaves))
+            return fail(SRA_EINVAL, "segment %d: null buffer", s);
+        int kmax = 0;
+        if ((r = kmax_for(n, o, 3, &kmax))) return r;
+        RangeCfg cfg;
+        if ((r = make_cfg(n, o, kmax, 4, o->block_threads > 0 ? o->block_threads : 256, &cfg))) return r;
+        cfg.threads = cfg.NB * cfg.H;
+        kmaxes[s] = kmax;
+        BatchSegDev &D = ds[s];
+        memset(&D, 0, sizeof D);
+        D.net = n->dev;
+        D.cfg = cfg;
+        D.src.kind = SRC_NODES;
+        D.src.nodes = in + g.first;
+        D.src.n = g.n;
+        D.src.split = o->split;
+        memcpy(D.src.kd_n3, n3, sizeof n3);
+        for (int d = 0; d < 3; ++d) {
+            D.src.root_lo[d] = root_lo[d];
+            D.src.root_ext[d] = root_hi[d] - root_lo[d];
+        }
+        double per_box = 0;
+        for (int l = 0; l < n->L; ++l) per_box += (double)n->widths[l] * n->widths[l + 1] * (kmax + 2);
+        chunk_cost[s] = per_box * cfg.NB;
+        BatchSplitSeg &S = ss[s];
+        memset(&S, 0, sizeof S);
+        S.first = g.first;
+        S.n = g.n;
+        S.out_first = g.out_first;
+        S.cap_out = g.cap_out;
+        S.leaf_first = g.leaf_first;
+        S.cap_leaves = g.cap_leaves;
+        S.blk0 = nblk;
+        S.max_level = g.max_level;
+        S.split = o->split;
+        memcpy(S.kd_axis, axis, sizeof axis);
+        nblk += split_blocks(g.n);
+        if (g.first + g.n > cls_n) cls_n = g.first + g.n;
+    }
+    // launches: one per noise-column bound, segments heaviest chunk first
+    std::vector<int> kinds;
+    for (int s = 0; s < n_segs; ++s)
+        if (segs[s].n > 0 && std::find(kinds.begin(), kinds.end(), kmaxes[s]) == kinds.end()) kinds.push_back(kmaxes[s]);
+    std::vector<int> order;
+    struct Launch { int kmax, off, cnt, threads, smem; long long chunks; };
+    std::vector<Launch> launches;
+    for (int km : kinds) {
+        Launch L = {km, (int)order.size(), 0, 0, 0, 0};
+        std::vector<int> mine;
+        for (int s = 0; s < n_segs; ++s)
+            if (segs[s].n > 0 && kmaxes[s] == km) mine.push_back(s);
+        std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
+        for (int s : mine) {
+            ds[s].chunk0 = L.chunks;
+            L.chunks += (segs[s].n + ds[s].cfg.NB - 1) / ds[s].cfg.NB;
+            L.threads = std::max(L.threads, ds[s].cfg.threads);
+            L.smem = std::max(L.smem, ds[s].cfg.NB * ds[s].cfg.slot_bytes);
+            order.push_back(s);
+        }
+        L.cnt = (int)mine.size();
+        launches.push_back(L);
+    }
+    const size_t b_cls = align16((size_t)cls_n), b_blk = align16((size_t)nblk * 16),
+                 b_ds = align16(ds.size() * sizeof(BatchSegDev)), b_ss = align16(ss.size() * sizeof(BatchSplitSeg)),
+                 b_ord = align16((order.size() + 1) * sizeof(int)), b_next = align16(launches.size() * 8 + 8);
+    Scratch sc;
+    if ((r = scratch_alloc(sc, b_cls + b_blk + b_ds + b_ss + b_ord + b_next, st))) return r;
+    char *base = (char *)sc.p;
+    uint8_t *cls = (uint8_t *)base;
+    long long *blk = (long long *)(base + b_cls);
+    BatchSegDev *dsd = (BatchSegDev *)(base + b_cls + b_blk);
+    BatchSplitSeg *ssd = (BatchSplitSeg *)(base + b_cls + b_blk + b_ds);
+    int *ordd = (int *)(base + b_cls + b_blk + b_ds + b_ss);
+    unsigned long long *next = (unsigned long long *)(base + b_cls + b_blk + b_ds + b_ss + b_ord);
+    for (int s = 0; s < n_segs; ++s) ds[s].out.cls = cls + segs[s].first;
+    SRA_CK(cudaMemcpyAsync(dsd, ds.data(), ds.size() * sizeof(BatchSegDev), cudaMemcpyHostToDevice, st));
+    SRA_CK(cudaMemcpyAsync(ssd, ss.data(), ss.size() * sizeof(BatchSplitSeg), cudaMemcpyHostToDevice, st));
+    if (!order.empty())
+        SRA_CK(cudaMemcpyAsync(ordd, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    SRA_CK(cudaMemsetAsync(next, 0, launches.size() * 8 + 8, st));
+    // the host arrays are copied before these calls return (pageable sources)
+    for (size_t k = 0; k < launches.size(); ++k) {
+        const Launch &L = launches[k];
+        cudaError_t e = launch_multi_bound_f32(L.kmax, dsd, ordd + L.off, L.cnt, L.chunks, next + k, L.threads,
+                                               L.smem, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "batched bound launch (K <= %d): %s", L.kmax, cudaGetErrorString(e));
+    }
+    cudaError_t e = launch_split_batch(cls, in, ssd, n_segs, nblk, out, leaves, (unsigned long long *)counts, blk, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "batched split launch: %s", cudaGetErrorString(e));
     return SRA_OK;
 }
 

@@ -59,6 +59,30 @@ cudaError_t launch_rays_f32(int kmax, const NetDev &net, const void *rp, const R
     return cudaErrorInvalidValue;
 }
 
+template <typename T, int KMAX>
+static cudaError_t launch_multi_t(const BatchSegDev *segs, const int *order, int nseg, long long nchunks,
+                                  unsigned long long *next, int threads, int smem, cudaStream_t st) {
+    auto k = multi_bound_kernel<T, KMAX>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem)) != cudaSuccess) return e;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long grid = (long long)(per_sm > 0 ? per_sm : 1) * sms;
+    if (grid > nchunks) grid = nchunks;
+    if (grid < 1) return cudaSuccess;
+    k<<<(unsigned)grid, threads, smem, st>>>(segs, order, nseg, nchunks, next);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_multi_bound_f32(int kmax, const BatchSegDev *segs, const int *order, int nseg,
+                                   long long nchunks, unsigned long long *next, int threads, int smem,
+                                   cudaStream_t st) {
+    SRA_KMAX_SWITCH(launch_multi_t, segs, order, nseg, nchunks, next, threads, smem, st)
+    return cudaErrorInvalidValue;
+}
+
 int rays_blocks_per_sm_f32(int kmax, const RangeCfg &cfg) {
     SRA_KMAX_SWITCH(rays_occ, cfg)
     return 1;

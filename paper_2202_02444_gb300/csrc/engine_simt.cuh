@@ -216,7 +216,7 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
             row[KMAX + 1] = r.xi;
             row[KMAX + 2] = r.p;
         }
-        __syncthreads();
+        engine_sync(cfg);
         return Ncur;
     }
     const int C = Ncur + Cnew;
@@ -231,13 +231,13 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
             if (lane == 0) s.part[warp * (KMAX + 4) + k] = v;
         }
         if (valid && newsym) s.score[Ncur + new_idx] = fabs(gamma);
-        __syncthreads();
+        engine_sync(cfg);
         for (int k = i; k < Ncur; k += cfg.H) {
             T v = T(0);
             for (int w = 0; w < nwarps; ++w) v += s.part[w * (KMAX + 4) + k];
             s.score[k] = v;
         }
-        __syncthreads();
+        engine_sync(cfg);
         for (int c = i; c < C; c += cfg.H) {
             const T sc = s.score[c];
             int rank = 0;
@@ -247,7 +247,7 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
             }
             s.keep[c] = rank < Knew;
         }
-        __syncthreads();
+        engine_sync(cfg);
         if (i < 32) {  // one warp lists kept candidates in order
             int base = 0;
             for (int c0 = 0; c0 < C; c0 += 32) {
@@ -258,7 +258,7 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
                 base += __popc(m);
             }
         }
-        __syncthreads();
+        engine_sync(cfg);
     }
     if (valid) {
         T *row = s.X + i * RS;
@@ -283,7 +283,7 @@ __device__ int condense_and_store(Row<T, KMAX> &r, T gamma, bool valid, bool new
         row[KMAX + 1] = r.xi + dropped;
         row[KMAX + 2] = r.p;
     }
-    __syncthreads();
+    engine_sync(cfg);
     return Knew;
 }
 
@@ -340,7 +340,7 @@ __device__ int posenc_layer(const NetDev &net, const RangeCfg &cfg, const Slot<T
             if (PT) r.p = sinpi_t(r.p);
         }
     }
-    __syncthreads();  // every read of the input rows is done
+    engine_sync(cfg);  // every read of the input rows is done
     return condense_and_store<T, KMAX, PT>(r, gamma, valid, i >= 3, i - 3, 6 * net.pe, Ncur, cfg, s, i);
 }
 
@@ -354,7 +354,7 @@ __device__ void propagate(const NetDev &net, const RangeCfg &cfg, const Slot<T> 
         const bool valid = i < Ld.out;
         Row<T, KMAX> r;
         if (valid) matmul_row<T, KMAX, PT>(Ld, s.X, i, r);
-        __syncthreads();  // input rows consumed
+        engine_sync(cfg);  // input rows consumed
         T gamma = T(0);
         if (valid) gamma = activate_row<T, KMAX, PT>(Ld.act, cfg, r);
         const bool nl = Ld.act != SRA_ACT_IDENTITY;
@@ -379,7 +379,7 @@ __device__ void propagate(const NetDev &net, const RangeCfg &cfg, const Slot<T> 
         }
         s.outv[k] = acc;
     }
-    __syncthreads();
+    engine_sync(cfg);
     if (i == 0) {
         const T b0 = __ldg(b_of<T>(Lo));
         T rad = T(0);
@@ -391,7 +391,7 @@ __device__ void propagate(const NetDev &net, const RangeCfg &cfg, const Slot<T> 
         s.outv[1] = rad;
         s.outv[2] = pv;
     }
-    __syncthreads();
+    engine_sync(cfg);
 }
 
 // Initial affine form of a box: x0 = c, X = diag(h), x_inf = 0 (Proc. 1;
@@ -415,6 +415,50 @@ __device__ __forceinline__ void init_box_rows(const RangeCfg &cfg, const Slot<T>
 }
 
 // ---------------------------------------------------------------------------
+// RangeBound (Proc. 1) of group g: boxes g * NB + slot of src, one per slot
+// of cfg.H threads. Called by every engine thread of the CTA.
+template <typename T, int KMAX>
+__device__ __forceinline__ void bound_group(const NetDev &net, const BoxSrc &src, const BoundOut &out,
+                                            const RangeCfg &cfg, const Slot<T> &s, int slot, int i,
+                                            long long g, long long n) {
+    const long long b = g * cfg.NB + slot;
+    const bool active = b < n;
+    const long long gb = active ? (src.list ? (long long)src.list[b] : b) : 0;
+
+    T c[3] = {T(0), T(0), T(0)}, h[3] = {T(0), T(0), T(0)};
+    if (active && i < 3) {
+        if (src.kind == SRC_NODES) {
+            node_geometry<T>(src, src.nodes[gb], c, h);
+        } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                c[d] = T(src.centers[gb * 3 + d]);
+                h[d] = (src.kind == SRC_BOXES) ? T(src.halfw[gb * 3 + d]) : T(0);
+            }
+        }
+    }
+    init_box_rows<T, KMAX>(cfg, s, i, c, h, (const T *)nullptr);
+    int Ncur = (cfg.arith == SRA_ARITH_INTERVAL) ? 0 : 3;
+    engine_sync(cfg);
+    if (net.pe) Ncur = posenc_layer<T, KMAX, false>(net, cfg, s, i, Ncur);
+    propagate<T, KMAX, false>(net, cfg, s, i, Ncur);
+    if (i == 0 && active) {
+        const T y0 = s.outv[0], rad = s.outv[1];
+        const T lo = y0 - rad, hi = y0 + rad;
+        const int k = classify_range(lo, hi);
+        if (out.lo) out.lo[gb] = (float)lo;
+        if (out.hi) out.hi[gb] = (float)hi;
+        if (out.cls) out.cls[gb] = (uint8_t)k;
+        if (out.recheck_counter) atomicAdd(out.recheck_counter, 1ull);
+        if (out.flag_list) {  // either end of the range near zero: FP64 decides
+            const T band = T(out.band) * (fabs(y0) + rad);
+            if (fabs(lo) <= band || fabs(hi) <= band)
+                out.flag_list[atomicAdd(out.flag_count, 1)] = (int)gb;
+        }
+    }
+    engine_sync(cfg);  // outv / X reuse by the next group
+}
+
 // Bound kernel: RangeBound (Proc. 1) for boxes, tree nodes or points.
 template <typename T, int KMAX>
 __global__ void __launch_bounds__(MaxThreads<T, KMAX>::value)
@@ -425,43 +469,40 @@ bound_kernel(NetDev net, BoxSrc src, BoundOut out, RangeCfg cfg) {
     long long n = src.n;
     if (src.list) n = *src.list_count;
     // grid-stride over groups of NB boxes (CTA-uniform trip count)
-    for (long long g = blockIdx.x; g * cfg.NB < n; g += gridDim.x) {
-        const long long b = g * cfg.NB + slot;
-        const bool active = b < n;
-        const long long gb = active ? (src.list ? (long long)src.list[b] : b) : 0;
+    for (long long g = blockIdx.x; g * cfg.NB < n; g += gridDim.x)
+        bound_group<T, KMAX>(net, src, out, cfg, s, slot, i, g, n);
+}
 
-        T c[3] = {T(0), T(0), T(0)}, h[3] = {T(0), T(0), T(0)};
-        if (active && i < 3) {
-            if (src.kind == SRC_NODES) {
-                node_geometry<T>(src, src.nodes[gb], c, h);
-            } else {
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    c[d] = T(src.centers[gb * 3 + d]);
-                    h[d] = (src.kind == SRC_BOXES) ? T(src.halfw[gb * 3 + d]) : T(0);
-                }
-            }
-        }
-        init_box_rows<T, KMAX>(cfg, s, i, c, h, (const T *)nullptr);
-        int Ncur = (cfg.arith == SRA_ARITH_INTERVAL) ? 0 : 3;
+// Persistent RangeBound over the frontiers of many networks (one launch per
+// noise-column bound KMAX): each CTA takes the next chunk from a global
+// counter, finds its segment and runs that network's layout with the first
+// NB * H threads; the others wait for the next chunk. Segments are listed
+// heaviest first, so the long chunks start early.
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(MaxThreads<T, KMAX>::value)
+multi_bound_kernel(const BatchSegDev *segs, const int *order, int nseg, long long nchunks,
+                   unsigned long long *next) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ long long s_chunk;
+    for (;;) {
+        if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(next, 1ull);
         __syncthreads();
-        if (net.pe) Ncur = posenc_layer<T, KMAX, false>(net, cfg, s, i, Ncur);
-        propagate<T, KMAX, false>(net, cfg, s, i, Ncur);
-        if (i == 0 && active) {
-            const T y0 = s.outv[0], rad = s.outv[1];
-            const T lo = y0 - rad, hi = y0 + rad;
-            const int k = classify_range(lo, hi);
-            if (out.lo) out.lo[gb] = (float)lo;
-            if (out.hi) out.hi[gb] = (float)hi;
-            if (out.cls) out.cls[gb] = (uint8_t)k;
-            if (out.recheck_counter) atomicAdd(out.recheck_counter, 1ull);
-            if (out.flag_list) {  // either end of the range near zero: FP64 decides
-                const T band = T(out.band) * (fabs(y0) + rad);
-                if (fabs(lo) <= band || fabs(hi) <= band)
-                    out.flag_list[atomicAdd(out.flag_count, 1)] = (int)gb;
-            }
+        const long long c = s_chunk;
+        __syncthreads();  // read before thread 0 takes the next chunk
+        if (c >= nchunks) break;
+        int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (segs[order[mid]].chunk0 <= c) lo = mid;
+            else hi = mid - 1;
         }
-        __syncthreads();  // outv / X reuse by the next group
+        const BatchSegDev &S = segs[order[lo]];
+        const RangeCfg cfg = S.cfg;
+        if ((int)threadIdx.x < cfg.threads) {
+            const int slot = threadIdx.x / cfg.H, i = threadIdx.x - slot * cfg.H;
+            const Slot<T> s = carve<T>(smem, slot, cfg);
+            bound_group<T, KMAX>(S.net, S.src, S.out, cfg, s, slot, i, c - S.chunk0, S.src.n);
+        }
     }
 }
 

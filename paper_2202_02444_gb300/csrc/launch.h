@@ -43,4 +43,22 @@ struct SplitArgs {
 cudaError_t launch_split(const SplitArgs &a, cudaStream_t st);
 long long split_blocks(long long n);
 
+// Batched round over many networks: the persistent multi-network bound
+// kernel (one launch per KMAX) and the segmented split.
+cudaError_t launch_multi_bound_f32(int kmax, const BatchSegDev *segs, const int *order, int nseg,
+                                   long long nchunks, unsigned long long *next, int threads, int smem,
+                                   cudaStream_t st);
+struct BatchSplitSeg {
+    long long first, n;          // nodes in[first, first + n) and their classes
+    long long out_first, cap_out;
+    long long leaf_first, cap_leaves;
+    long long blk0;              // first split block of the segment
+    int max_level, split;
+    unsigned char kd_axis[kMaxKdLevels];
+};
+// counts: device int64[nseg][SRA_CNT_N]; blk: scratch 2 * nblk
+cudaError_t launch_split_batch(const uint8_t *cls, const sra_node *in, const BatchSplitSeg *segs, int nseg,
+                               long long nblk, sra_node *out, sra_node *leaves, unsigned long long *counts,
+                               long long *blk, cudaStream_t st);
+
 }  // namespace sra

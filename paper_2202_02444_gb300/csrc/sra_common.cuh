@@ -76,6 +76,25 @@ struct RangeCfg {
     int rows;   // rows of the per-box state matrix (max width)
     int slot_bytes;
     int x_off, score_off, part_off, outv_off, keep_off, src_off, ray_off;
+    int threads;  // threads that run the engine on this layout: 0 = the whole
+                  // CTA (__syncthreads), else the first `threads` (named barrier 1)
+};
+
+// The barrier of the SIMT engine: the whole CTA, or the first cfg.threads
+// threads (whole warps) when a CTA runs layouts of several networks.
+__device__ __forceinline__ void engine_sync(const RangeCfg &cfg) {
+    if (cfg.threads == 0) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"r"(cfg.threads) : "memory");
+}
+
+// One segment of a batched round over many networks: a network, its
+// layout, its nodes and where their classes go.
+struct BatchSegDev {
+    NetDev net;
+    RangeCfg cfg;      // cfg.threads = NB * H engine threads
+    BoxSrc src;        // SRC_NODES, this segment's nodes
+    BoundOut out;      // classes of this segment's nodes
+    long long chunk0;  // first chunk (group of NB nodes) of the segment in its launch
 };
 
 // CastRay (Proc. 2) launch parameters and per-slot state.

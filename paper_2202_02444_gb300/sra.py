@@ -49,7 +49,8 @@ class Opts(C.Structure):
                 ("precision", C.c_int32), ("recheck", C.c_int32), ("recheck_band", C.c_float),
                 ("split", C.c_int32), ("delta", C.c_float), ("t_max", C.c_float),
                 ("sigma0", C.c_float), ("eta_plus", C.c_float), ("eta_minus", C.c_float),
-                ("safety", C.c_float), ("max_iters", C.c_int64)]
+                ("safety", C.c_float), ("max_iters", C.c_int64),
+                ("block_threads", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -69,6 +70,13 @@ class ServeCfg(C.Structure):
 
 REQ_RAYS, REQ_BOXES, REQ_LEAVES = 0, 1, 2
 
+
+class BatchSeg(C.Structure):
+    """One network's frontier in a batched round (sra_batch_seg)."""
+    _fields_ = [("net", C.c_int32), ("max_level", C.c_int32), ("first", C.c_int64), ("n", C.c_int64),
+                ("out_first", C.c_int64), ("cap_out", C.c_int64), ("leaf_first", C.c_int64),
+                ("cap_leaves", C.c_int64)]
+
 _vp = C.c_void_p
 _lib.sra_last_error.restype = C.c_char_p
 _lib.sra_default_opts.argtypes = [C.POINTER(Opts)]
@@ -84,10 +92,14 @@ _lib.sra_extract_leaves.argtypes = [_vp, C.POINTER(Opts), C.POINTER(C.c_float),
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]
 _lib.sra_eval.argtypes = [_vp, _vp, C.c_int64, _vp, _vp]
 _lib.sra_sync_status.argtypes = [_vp, _vp]
+_lib.sra_classify_and_split_batch.argtypes = [C.POINTER(_vp), C.POINTER(Opts), C.c_int32,
+                                              C.POINTER(C.c_float), C.POINTER(C.c_float), _vp,
+                                              C.POINTER(BatchSeg), C.c_int32, _vp, _vp, _vp, _vp]
 _lib.sra_serve.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(Opts), C.c_int32,
                            C.POINTER(ServeCfg), C.POINTER(Request), C.c_int64]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
-           "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve"):
+           "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve",
+           "sra_classify_and_split_batch"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -103,7 +115,7 @@ def _check(code):
 
 def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=False,
               recheck_band=1e-5, split="octree", delta=None, t_max=None, sigma0=None,
-              eta_plus=None, eta_minus=None, safety=None, max_iters=None):
+              eta_plus=None, eta_minus=None, safety=None, max_iters=None, block_threads=0):
     o = Opts()
     _lib.sra_default_opts(C.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -121,6 +133,7 @@ def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=F
         o.sigma0 = float(t_max) / 10.0
     if max_iters is not None:
         o.max_iters = int(max_iters)
+    o.block_threads = int(block_threads)
     return o
 
 
@@ -233,6 +246,26 @@ def classify_and_split(net, frontier, max_level, root_lo=(-1.0, -1.0, -1.0),
                                        int(max_level), _ptr(out), int(cap_out), _ptr(leaves),
                                        int(cap_leaves), _ptr(counts), _stream()))
     return out, leaves, counts
+
+
+def classify_and_split_batch(nets, opts, frontier, segs, out, leaves, counts=None,
+                             root_lo=(-1.0, -1.0, -1.0), root_hi=(1.0, 1.0, 1.0)):
+    """One round of Proc. 3 over many networks' frontiers (sra_classify_and_split_batch).
+    nets / opts: one option set per network; frontier, out, leaves: CUDA int16
+    [*, 4] node tensors; segs: BatchSeg list (or dicts of its fields).
+    Returns counts, a CUDA int64 [len(segs), 8] tensor."""
+    _need(frontier, torch.int16, 4, "frontier")
+    segs = [s if isinstance(s, BatchSeg) else BatchSeg(**s) for s in segs]
+    dev = frontier.device
+    if counts is None:
+        counts = torch.zeros((len(segs), CNT_N), dtype=torch.int64, device=dev)
+    handles = (_vp * len(nets))(*[n.handle for n in nets])
+    fo = (Opts * len(opts))(*opts)
+    sg = (BatchSeg * len(segs))(*segs)
+    _check(_lib.sra_classify_and_split_batch(handles, fo, len(nets), (C.c_float * 3)(*root_lo),
+                                             (C.c_float * 3)(*root_hi), _ptr(frontier), sg, len(segs),
+                                             _ptr(out), _ptr(leaves), _ptr(counts), _stream()))
+    return counts
 
 
 def cast_rays(net, origins, dirs, opts=None, t_hit=None, iters=None, **kw):
