@@ -79,6 +79,8 @@ def parse_args():
     ap.add_argument("--serve-rates", default="2,8", help="request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-cap", type=int, default=100_000, help="frontier cap per net per level")
     ap.add_argument("--cpu-sample", type=int, default=2048, help="oracle boxes for cpu_baseline")
     ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
     return ap.parse_args()
@@ -236,6 +238,50 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
     for n in nets:
         n.close()
     return out
+
+
+def batched_phase(sra, torch, cap):
+    """64 uneven networks (widths 32..512, depths 3..10, ReLU / ELU / SIREN sin,
+    octree depths 8..11; generator seeds 1000..1063): autotune K and the CTA
+    shape per network, then build every tree level by level with one batched
+    round per level (sra_classify_and_split_batch), against the same trees
+    built one network and one level at a time."""
+    from paper_2202_02444_gb300 import autotune, batch
+    mlps = [wl.net_batch_mix(i) for i in range(64)]
+    nets = [sra.Net(m) for m in mlps]
+    depths = [int(m.meta["octree_depth"]) for m in mlps]
+    t0 = time.perf_counter()
+    tuned = [autotune.tune(n, m, d, probe_level=4, sample=2048, reps=2) for m, n, d in zip(mlps, nets, depths)]
+    t_tune = time.perf_counter() - t0
+    opts = [sra.make_opts(arith="truncate", K=r["K"], block_threads=r["block_threads"]) for r in tuned]
+    batch.build_trees(nets[:4], opts[:4], [2] * 4, cap=cap)  # warm-up of the launch paths
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res, rounds = batch.build_trees(nets, opts, depths, cap=cap)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res1 = batch.build_trees_one_by_one(nets, opts, depths, cap=cap)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter() - t0
+    nodes = sum(r["nodes"] for r in res)
+    flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
+    same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
+    for n in nets:
+        n.close()
+    ks = {}
+    for t in tuned:
+        ks[str(t["K"])] = ks.get(str(t["K"]), 0) + 1
+    return {"workload": "64 nets of the uneven generator (seeds 1000..1063): width U{32..512}, depth "
+                        "U[3,10], ReLU/ELU/SIREN-sin, octree depth U[8,11]; affine-truncate FP32 with K and "
+                        f"threads per CTA autotuned per net; frontier cap {cap} nodes per net per level",
+            "box_evals": nodes, "rounds": rounds,
+            "batched_s": tb, "batched_evals_per_s": nodes / tb, "batched_tflops": flop / tb / 1e12,
+            "one_by_one_s": t1, "one_by_one_evals_per_s": nodes / t1,
+            "batched_vs_one_by_one": t1 / tb, "same_trees": same,
+            "nets_truncated_at_cap": int(sum(r["truncated"] for r in res)),
+            "autotune_s": t_tune, "autotune_K": ks,
+            "wall_clock_note": "host-timed with synchronisation (one counter read per level)"}
 
 
 def make_frontier(sra, net, level, batch, opts):
@@ -494,6 +540,9 @@ def main():
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
     agree[fin] &= np.abs(ta[fin] - tb[fin]) <= 1e-4 * 1.0001 + 1e-6
 
+    batched = None
+    if not args.no_batched and rank == 0:
+        batched = batched_phase(sra, torch, args.batched_cap)
     serving = None
     if not args.no_serve and rank == 0:
         rates = [float(x) for x in args.serve_rates.split(",") if x]
@@ -553,6 +602,7 @@ def main():
                      "same_outcome_frac": float(agree.mean()),
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
                      / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
+            "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clocks,

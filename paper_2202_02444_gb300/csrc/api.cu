@@ -391,6 +391,61 @@ void prepare_tc_rays(sra_net *n, const float *params) {
     n->tcr_ok = true;
 }
 
+// Streams the library forks work onto (per device, created on first use and
+// kept for the process lifetime).
+constexpr int kPoolStreams = 8;
+std::mutex g_pool_mu;
+std::vector<cudaStream_t> g_pool[64];
+
+cudaStream_t pool_stream(int k) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    std::vector<cudaStream_t> &p = g_pool[dev & 63];
+    while ((int)p.size() < kPoolStreams) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        p.push_back(s);
+    }
+    return p.empty() ? nullptr : p[k % p.size()];
+}
+
+// Run n pieces of work concurrently: piece q is enqueued by f(q, stream) on a
+// pooled stream that first waits for everything already on st; st then waits
+// for all pieces. With one piece (or no pool) everything goes on st.
+template <typename F> sra_status fork_join(cudaStream_t st, int n, F &&f) {
+    if (n <= 1 || !pool_stream(0)) {
+        for (int q = 0; q < n; ++q) {
+            sra_status r = f(q, st);
+            if (r) return r;
+        }
+        return SRA_OK;
+    }
+    cudaEvent_t fork = nullptr;
+    SRA_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    SRA_CK(cudaEventRecord(fork, st));
+    sra_status status = SRA_OK;
+    const int used = n < kPoolStreams ? n : kPoolStreams;
+    for (int q = 0; q < n && status == SRA_OK; ++q) {
+        cudaStream_t ls = pool_stream(q);
+        if (q < used && cudaStreamWaitEvent(ls, fork, 0) != cudaSuccess) status = fail(SRA_ECUDA, "fork wait");
+        if (status == SRA_OK) status = f(q, ls);
+    }
+    for (int q = 0; q < used; ++q) {  // join every stream that received work
+        cudaEvent_t j = nullptr;
+        if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(j, pool_stream(q)) != cudaSuccess || cudaStreamWaitEvent(st, j, 0) != cudaSuccess) {
+            if (status == SRA_OK) status = fail(SRA_ECUDA, "join");
+        }
+        if (j) cudaEventDestroy(j);
+    }
+    cudaEventDestroy(fork);
+    return status;
+}
+
 }  // namespace
 
 sra_status sra::set_error(sra_status s, const char *fmt, ...) {
@@ -734,22 +789,27 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
         nblk += split_blocks(g.n);
         if (g.first + g.n > cls_n) cls_n = g.first + g.n;
     }
-    // launches: one per noise-column bound, segments heaviest chunk first
-    std::vector<int> kinds;
-    for (int s = 0; s < n_segs; ++s)
-        if (segs[s].n > 0 && std::find(kinds.begin(), kinds.end(), kmaxes[s]) == kinds.end()) kinds.push_back(kmaxes[s]);
+    // launches: one per (noise-column bound, CTA shape), segments heaviest
+    // chunk first; the launches run concurrently on pooled streams
+    std::vector<std::pair<int, int>> kinds;
+    for (int s = 0; s < n_segs; ++s) {
+        const std::pair<int, int> key(kmaxes[s], ds[s].cfg.threads);
+        if (segs[s].n > 0 && std::find(kinds.begin(), kinds.end(), key) == kinds.end()) kinds.push_back(key);
+    }
     std::vector<int> order;
-    struct Launch { int kmax, off, cnt, threads, smem; long long chunks; };
+    struct Launch { int kmax, off, cnt, threads, smem; long long chunks; double work; };
     std::vector<Launch> launches;
-    for (int km : kinds) {
-        Launch L = {km, (int)order.size(), 0, 0, 0, 0};
+    for (const auto &kk : kinds) {
+        const int km = kk.first;
+        Launch L = {km, (int)order.size(), 0, 0, 0, 0, 0.0};
         std::vector<int> mine;
         for (int s = 0; s < n_segs; ++s)
-            if (segs[s].n > 0 && kmaxes[s] == km) mine.push_back(s);
+            if (segs[s].n > 0 && kmaxes[s] == km && ds[s].cfg.threads == kk.second) mine.push_back(s);
         std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
         for (int s : mine) {
             ds[s].chunk0 = L.chunks;
             L.chunks += (segs[s].n + ds[s].cfg.NB - 1) / ds[s].cfg.NB;
+            L.work += chunk_cost[s] * (double)((segs[s].n + ds[s].cfg.NB - 1) / ds[s].cfg.NB);
             L.threads = std::max(L.threads, ds[s].cfg.threads);
             L.smem = std::max(L.smem, ds[s].cfg.NB * ds[s].cfg.slot_bytes);
             order.push_back(s);
@@ -776,12 +836,21 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
         SRA_CK(cudaMemcpyAsync(ordd, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SRA_CK(cudaMemsetAsync(next, 0, launches.size() * 8 + 8, st));
     // the host arrays are copied before these calls return (pageable sources)
-    for (size_t k = 0; k < launches.size(); ++k) {
-        const Launch &L = launches[k];
-        cudaError_t e = launch_multi_bound_f32(L.kmax, dsd, ordd + L.off, L.cnt, L.chunks, next + k, L.threads,
-                                               L.smem, st);
-        if (e != cudaSuccess) return fail(SRA_ECUDA, "batched bound launch (K <= %d): %s", L.kmax, cudaGetErrorString(e));
-    }
+    // heaviest launch first: the lighter ones fill the SMs its tail frees
+    std::vector<size_t> lorder(launches.size());
+    for (size_t k = 0; k < lorder.size(); ++k) lorder[k] = k;
+    std::stable_sort(lorder.begin(), lorder.end(),
+                     [&](size_t a, size_t b) { return launches[a].work > launches[b].work; });
+    if ((r = fork_join(st, (int)launches.size(), [&](int q, cudaStream_t ls) -> sra_status {
+             const size_t k = lorder[q];
+             const Launch &L = launches[k];
+             cudaError_t e = launch_multi_bound_f32(L.kmax, dsd, ordd + L.off, L.cnt, L.chunks, next + k,
+                                                    L.threads, L.smem, ls);
+             if (e != cudaSuccess)
+                 return fail(SRA_ECUDA, "batched bound launch (K <= %d): %s", L.kmax, cudaGetErrorString(e));
+             return SRA_OK;
+         })))
+        return r;
     cudaError_t e = launch_split_batch(cls, in, ssd, n_segs, nblk, out, leaves, (unsigned long long *)counts, blk, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "batched split launch: %s", cudaGetErrorString(e));
     return SRA_OK;
