@@ -540,6 +540,26 @@ def main():
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
     agree[fin] &= np.abs(ta[fin] - tb[fin]) <= 1e-4 * 1.0001 + 1e-6
 
+    # mesh phase: marching tetrahedra in level-7 octree cells of the 256x8 net,
+    # 2^3 cells per leaf axis (1024^3 effective resolution, the meshing step
+    # the level-10 octree of this network feeds)
+    mesh = None
+    if rank == 0:
+        nl = min(16384, B)
+        ml = fr[:nl].contiguous()
+        sra.mesh_leaves(net_box, ml[:64], 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tris = sra.mesh_leaves(net_box, ml, 3)
+        torch.cuda.synchronize()
+        mt = time.perf_counter() - t0
+        mesh = {"workload": f"{nl} level-7 frontier cells of ReLU 3-[256]x8-1, 8^3 sub-cells each "
+                            "(1024^3 effective grid), marching tetrahedra",
+                "leaves": nl, "triangles": int(tris.shape[0]), "s": mt,
+                "leaves_per_s": nl / mt, "point_evals_per_s": nl * 729 / mt,
+                "timing": "host clock around one synchronous sra_mesh_leaves call"}
+        del tris
+
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_phase(sra, torch, args.batched_cap)
@@ -602,6 +622,7 @@ def main():
                      "same_outcome_frac": float(agree.mean()),
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
                      / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
+            "mesh": mesh,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -252,6 +252,23 @@ sra_status sra_extract_leaves(const sra_net *net, const sra_opts *opts, const fl
                               int64_t cap, int64_t *n_leaves, int64_t *level_counts,
                               void *stream);
 
+/* Mesh of the zero level set inside octree leaves: the dense bottom of
+ * hierarchical mesh extraction (Sec. 4.7). Each leaf (device sra_node[n],
+ * e.g. the UNKNOWN leaves of sra_extract_leaves) is split into 2^sub_levels
+ * cells per axis (0 <= sub_levels <= 5); f is evaluated at the cell corners
+ * (FP32 forward pass) and every cell is cut into the six tetrahedra around
+ * its main diagonal, each meshed by marching tetrahedra (linear
+ * interpolation of f along the crossing edges). Leaves of one level give a
+ * closed, crack-free surface; a shared grid edge yields bit-identical
+ * vertices from every cell around it. Triangles face the f >= 0 side.
+ * tris_out (device float[cap][3][3]) is written in leaf, cell (x fastest),
+ * tetrahedron order; *n_tris (host) receives the triangle count. Errors:
+ * SRA_ECAPACITY when the count exceeds cap (the first cap are written),
+ * SRA_EINVAL, SRA_ENOMEM, SRA_ECUDA. Synchronises the stream once. */
+sra_status sra_mesh_leaves(const sra_net *net, const float *root_lo, const float *root_hi,
+                           const sra_node *leaves, int64_t n_leaves, int32_t sub_levels,
+                           float *tris_out, int64_t cap, int64_t *n_tris, void *stream);
+
 /* Plain forward evaluation f(x) for n points (device float[n][3] -> device
  * float[n]) in the network's FP32 weights. Asynchronous. */
 sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, void *stream);

@@ -650,6 +650,70 @@ sra_status sra_eval(const sra_net *n, const float *x, int64_t count, float *y, v
     return run_bound(n, &o, false, 1, src, out, count, as_stream(stream));
 }
 
+sra_status sra_mesh_leaves(const sra_net *n, const float *root_lo, const float *root_hi, const sra_node *leaves,
+                           int64_t n_leaves, int32_t sub_levels, float *tris, int64_t cap, int64_t *n_tris,
+                           void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if (!root_lo || !root_hi || !n_tris) return fail(SRA_EINVAL, "null root / n_tris");
+    for (int d = 0; d < 3; ++d)
+        if (!(root_hi[d] > root_lo[d])) return fail(SRA_EINVAL, "empty root box on axis %d", d);
+    if (sub_levels < 0 || sub_levels > 5) return fail(SRA_EINVAL, "sub_levels %d outside [0, 5]", sub_levels);
+    if (n_leaves < 0 || cap < 0) return fail(SRA_EINVAL, "negative size");
+    if ((n_leaves > 0 && !leaves) || (cap > 0 && !tris)) return fail(SRA_EINVAL, "null leaves / tris_out");
+    *n_tris = 0;
+    if (n_leaves == 0) return SRA_OK;
+    cudaStream_t st = as_stream(stream);
+    const long long G = (1 << sub_levels) + 1, per_leaf = G * G * G;
+    long long chunk = (1ll << 22) / per_leaf;
+    if (chunk < 1) chunk = 1;
+    if (chunk > n_leaves) chunk = n_leaves;
+    MeshArgs a;
+    memset(&a, 0, sizeof a);
+    a.sub = sub_levels;
+    for (int d = 0; d < 3; ++d) {
+        a.lo[d] = root_lo[d];
+        a.ext[d] = root_hi[d] - root_lo[d];
+    }
+    a.n = chunk;
+    const size_t b_pts = align16((size_t)chunk * per_leaf * 12), b_val = align16((size_t)chunk * per_leaf * 4),
+                 b_blk = align16((size_t)mesh_blocks(a) * 8);
+    Scratch sc;
+    if ((r = scratch_alloc(sc, b_pts + b_val + b_blk + 16, st))) return r;
+    float *pts = (float *)sc.p, *vals = (float *)((char *)sc.p + b_pts);
+    long long *blk = (long long *)((char *)sc.p + b_pts + b_val);
+    unsigned long long *counter = (unsigned long long *)((char *)sc.p + b_pts + b_val + b_blk);
+    SRA_CK(cudaMemsetAsync(counter, 0, 8, st));
+    sra_opts o;
+    sra_default_opts(&o);
+    o.arith = SRA_ARITH_INTERVAL;  // zero-width intervals: the plain forward pass of sra_eval
+    for (long long off = 0; off < n_leaves; off += chunk) {
+        a.leaves = leaves + off;
+        a.n = (n_leaves - off < chunk) ? n_leaves - off : chunk;
+        cudaError_t e = launch_mesh_points(a, pts, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "mesh points: %s", cudaGetErrorString(e));
+        BoxSrc src;
+        memset(&src, 0, sizeof src);
+        src.kind = SRC_POINTS;
+        src.centers = pts;
+        src.n = mesh_points(a);
+        BoundOut out;
+        memset(&out, 0, sizeof out);
+        out.lo = vals;
+        if ((r = run_bound(n, &o, false, 1, src, out, src.n, st))) return r;
+        e = launch_mesh_tris(a, vals, blk, counter, tris, cap, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "mesh triangles: %s", cudaGetErrorString(e));
+    }
+    unsigned long long total = 0;
+    SRA_CK(cudaMemcpyAsync(&total, counter, 8, cudaMemcpyDeviceToHost, st));
+    SRA_CK(cudaStreamSynchronize(st));
+    *n_tris = (int64_t)total;
+    if ((long long)total > cap)
+        return fail(SRA_ECAPACITY, "%llu triangles, capacity %lld", total, (long long)cap);
+    return SRA_OK;
+}
+
 sra_status sra_classify_and_split(const sra_net *n, const sra_opts *o, const float *root_lo,
                                   const float *root_hi, const sra_node *in, int64_t n_in,
                                   int32_t max_level, sra_node *out, int64_t cap_out,

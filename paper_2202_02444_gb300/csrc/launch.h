@@ -56,6 +56,19 @@ struct BatchSplitSeg {
     int max_level, split;
     unsigned char kd_axis[kMaxKdLevels];
 };
+// Mesh of the zero set inside leaves (marching tetrahedra on a 2^sub grid per leaf).
+struct MeshArgs {
+    const sra_node *leaves;
+    long long n;
+    int sub;
+    float lo[3], ext[3];
+};
+long long mesh_points(const MeshArgs &a);  // corner points of the leaves
+long long mesh_blocks(const MeshArgs &a);  // scan blocks of the cells
+cudaError_t launch_mesh_points(const MeshArgs &a, float *pts, cudaStream_t st);
+cudaError_t launch_mesh_tris(const MeshArgs &a, const float *vals, long long *blk, unsigned long long *counter,
+                             float *tris, long long cap, cudaStream_t st);
+
 // counts: device int64[nseg][SRA_CNT_N]; blk: scratch 2 * nblk
 cudaError_t launch_split_batch(const uint8_t *cls, const sra_node *in, const BatchSplitSeg *segs, int nseg,
                                long long nblk, sra_node *out, sra_node *leaves, unsigned long long *counts,

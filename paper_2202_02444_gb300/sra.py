@@ -95,11 +95,13 @@ _lib.sra_sync_status.argtypes = [_vp, _vp]
 _lib.sra_classify_and_split_batch.argtypes = [C.POINTER(_vp), C.POINTER(Opts), C.c_int32,
                                               C.POINTER(C.c_float), C.POINTER(C.c_float), _vp,
                                               C.POINTER(BatchSeg), C.c_int32, _vp, _vp, _vp, _vp]
+_lib.sra_mesh_leaves.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp, C.c_int64, C.c_int32,
+                                 _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
 _lib.sra_serve.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(Opts), C.c_int32,
                            C.POINTER(ServeCfg), C.POINTER(Request), C.c_int64]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
            "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve",
-           "sra_classify_and_split_batch"):
+           "sra_classify_and_split_batch", "sra_mesh_leaves"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -266,6 +268,23 @@ def classify_and_split_batch(nets, opts, frontier, segs, out, leaves, counts=Non
                                              (C.c_float * 3)(*root_hi), _ptr(frontier), sg, len(segs),
                                              _ptr(out), _ptr(leaves), _ptr(counts), _stream()))
     return counts
+
+
+def mesh_leaves(net, leaves, sub_levels=3, root_lo=(-1.0, -1.0, -1.0), root_hi=(1.0, 1.0, 1.0), cap=None):
+    """Marching-tetrahedra mesh of f = 0 inside the leaves (CUDA int16 [n,4]
+    nodes), 2^sub_levels cells per leaf axis; returns CUDA float32 [T,3,3]."""
+    _need(leaves, torch.int16, 4, "leaves")
+    n = leaves.shape[0]
+    cells = n * (1 << (3 * sub_levels))
+    cap = cap if cap is not None else max(1, 2 * cells)
+    tris = torch.empty((cap, 3, 3), dtype=torch.float32, device=leaves.device)
+    nt = C.c_int64(0)
+    code = _lib.sra_mesh_leaves(net.handle, (C.c_float * 3)(*root_lo), (C.c_float * 3)(*root_hi), _ptr(leaves), n,
+                                int(sub_levels), _ptr(tris), int(cap), C.byref(nt), _stream())
+    if code == ECAPACITY:
+        return mesh_leaves(net, leaves, sub_levels, root_lo, root_hi, cap=int(nt.value))
+    _check(code)
+    return tris[:nt.value]
 
 
 def cast_rays(net, origins, dirs, opts=None, t_hit=None, iters=None, **kw):
