@@ -69,8 +69,8 @@ def parse_args():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--batch", type=int, default=1 << 17, help="octree nodes per step")
     ap.add_argument("--frontier-level", type=int, default=7)
-    ap.add_argument("--ray-tile", type=int, default=32, help="ray tile side (tile^2 rays)")
-    ap.add_argument("--ray-iters", type=int, default=1500, help="per-ray iteration cap of the ray phase")
+    ap.add_argument("--ray-tile", type=int, default=64, help="ray tile side (tile^2 rays)")
+    ap.add_argument("--ray-iters", type=int, default=500, help="per-ray iteration cap of the ray phase")
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None,

@@ -337,6 +337,8 @@ void prepare_tc(sra_net *n, const float *params) {
 // Prepare the tensor-core ray kernel if the network has its shape: every
 // hidden width H in {128, 256, 512}, 1 <= L-2 <= 8 hidden H -> H layers, an
 // input width (after the positional encoding) of at most 64, scalar output.
+// Each layer becomes four BF16 matrices (W_b, W_r, |W_b|, sign(W_b) W_r);
+// layer 0's K is padded to 64 with zero columns.
 void prepare_tc_rays(sra_net *n, const float *params) {
     const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
     if (L < 3 || L - 2 > kMaxRayTc || (H != 128 && H != 256 && H != 512)) return;
@@ -344,40 +346,46 @@ void prepare_tc_rays(sra_net *n, const float *params) {
     for (int l = 1; l < L; ++l)
         if (n->widths[l] != H) return;
     const int nh = L - 2;
-    const size_t per = (size_t)H * H * 2;
-    const size_t bytes = 4 * nh * per + 256;
+    const size_t per_h = (size_t)H * H * 2, per_0 = (size_t)H * 64 * 2;
+    const size_t bytes = 4 * per_0 + 4 * nh * per_h + 256;
     if (cudaMalloc(&n->tcr_buf, bytes) != cudaSuccess) { n->tcr_buf = nullptr; cudaGetLastError(); return; }
-    std::vector<__nv_bfloat16> mats(4 * (size_t)H * H);
-    size_t off = (size_t)n->din * H + H;  // skip layer 0 (W0, b0)
     TcRayParams &t = n->tcrp;
     memset(&t, 0, sizeof t);
-    for (int l = 1; l <= nh; ++l) {
-        const float *W = params + off;
-        __nv_bfloat16 *wb = mats.data(), *wr = wb + (size_t)H * H, *wa = wr + (size_t)H * H,
-                      *ws = wa + (size_t)H * H;
-        for (size_t e = 0; e < (size_t)H * H; ++e) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
-            const float hf = __bfloat162float(h);
-            const __nv_bfloat16 r = __float2bfloat16_rn(W[e] - hf);
-            wb[e] = h;
-            wr[e] = r;
-            wa[e] = __float2bfloat16_rn(std::fabs(hf));
-            ws[e] = __float2bfloat16_rn(hf < 0.f ? -__bfloat162float(r) : __bfloat162float(r));
-        }
-        char *d = (char *)n->tcr_buf + 4 * (l - 1) * per;
-        if (cudaMemcpy(d, mats.data(), 4 * per, cudaMemcpyHostToDevice) != cudaSuccess ||
-            make_bf16_tile_map(&t.wb[l - 1], d, H, H, 128, 64) != 0 ||
-            make_bf16_tile_map(&t.wr[l - 1], d + per, H, H, 128, 64) != 0 ||
-            make_bf16_tile_map(&t.wa[l - 1], d + 2 * per, H, H, 128, 64) != 0 ||
-            make_bf16_tile_map(&t.ws[l - 1], d + 3 * per, H, H, 128, 64) != 0) {
-            cudaFree(n->tcr_buf);
-            n->tcr_buf = nullptr;
-            cudaGetLastError();
-            return;
-        }
+    // four matrices of one layer, from W [H][K_in] zero-padded to [H][K]
+    auto upload = [&](const float *W, int k_in, int K, char *dst, TcLayerMaps &maps) -> bool {
+        const size_t per = (size_t)H * K;
+        std::vector<__nv_bfloat16> m(4 * per);
+        for (int r = 0; r < H; ++r)
+            for (int k = 0; k < K; ++k) {
+                const float w = k < k_in ? W[(size_t)r * k_in + k] : 0.f;
+                const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                const float hf = __bfloat162float(h);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(w - hf);
+                const size_t e = (size_t)r * K + k;
+                m[e] = h;
+                m[per + e] = lo;
+                m[2 * per + e] = __float2bfloat16_rn(std::fabs(hf));
+                m[3 * per + e] = __float2bfloat16_rn(hf < 0.f ? -__bfloat162float(lo) : __bfloat162float(lo));
+            }
+        const size_t b = per * 2;
+        return cudaMemcpy(dst, m.data(), 4 * b, cudaMemcpyHostToDevice) == cudaSuccess &&
+               make_bf16_tile_map(&maps.wb, dst, H, K, 128, 64) == 0 &&
+               make_bf16_tile_map(&maps.wr, dst + b, H, K, 128, 64) == 0 &&
+               make_bf16_tile_map(&maps.wa, dst + 2 * b, H, K, 128, 64) == 0 &&
+               make_bf16_tile_map(&maps.ws, dst + 3 * b, H, K, 128, 64) == 0;
+    };
+    bool ok = upload(params, n->din, 64, (char *)n->tcr_buf, t.first);
+    size_t off = (size_t)n->din * H + H;  // layer 1 starts after W0, b0
+    for (int l = 1; ok && l <= nh; ++l) {
+        ok = upload(params + off, H, H, (char *)n->tcr_buf + 4 * per_0 + 4 * (l - 1) * per_h, t.hidden[l - 1]);
         off += (size_t)H * H + H;
     }
-    t.W0t = n->dev.layer[0].Wt;  // [din][H]
+    if (!ok) {
+        cudaFree(n->tcr_buf);
+        n->tcr_buf = nullptr;
+        cudaGetLastError();
+        return;
+    }
     for (int l = 0; l < L; ++l) t.b[l] = n->dev.layer[l].b;
     for (int l = 0; l + 1 < L; ++l) t.act[l] = n->acts[l];
     t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
@@ -385,7 +393,7 @@ void prepare_tc_rays(sra_net *n, const float *params) {
     t.L = L;
     t.din = n->din;
     t.pe = n->pe;
-    t.status = (int *)((char *)n->tcr_buf + 4 * nh * per);
+    t.status = (int *)((char *)n->tcr_buf + 4 * per_0 + 4 * nh * per_h);
     cudaMemset(t.status, 0, sizeof(int));
     n->tcr_H = H;
     n->tcr_ok = true;
@@ -969,7 +977,7 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
         p.safety = o->safety;
         p.max_iters = o->max_iters;
         long long grid = num_sms();
-        const long long need = (count + 7) / 8;
+        const long long need = (count + tc_ray_slots() - 1) / tc_ray_slots();
         if (grid > need) grid = need;
         cudaError_t e = launch_tc_rays(n->tcr_H, p, (int)grid, st);
         if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core ray kernel launch: %s", cudaGetErrorString(e));

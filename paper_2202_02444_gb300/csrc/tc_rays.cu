@@ -1,25 +1,31 @@
-// CastRay (Proc. 2) with the hidden layers on the tensor cores (tcgen05, BF16).
+// CastRay (Proc. 2) with every layer but the output one on the tensor cores
+// (tcgen05, split BF16).
 //
-// One persistent CTA per SM keeps NR = 8 ray slots in flight and refills a
+// One persistent CTA per SM keeps NR = 16 ray slots in flight and refills a
 // slot from a global counter when its ray ends. Every march step bounds each
 // slot's segment [t, t+sigma] with affine-fixed arithmetic (the one noise
 // symbol v = (sigma/2) r; every new symbol goes to x_inf, Sec. 3.3) and
 // evaluates f at p + (t+delta) r in the same pass (Proc. 2).
 //
-// Hidden layer l as two tensor-core products into TMEM (FP32 accumulation):
-//   D  = (W_b + W_r) [c_hi c_lo p_hi p_lo A_hi A_lo]     48 operand rows
-//   Dx = (|W_b| + sign(W_b) W_r) [x_hi x_lo]              16 operand rows
+// Linear layer l is two tensor-core products into TMEM (FP32 accumulation):
+//   D  = (W_b + W_r) [c_hi c_lo p_hi p_lo A_hi A_lo]     96 operand rows
+//   Dx = (|W_b| + sign(W_b) W_r) [x_hi x_lo]              32 operand rows
 // W = W_b + W_r is the BF16 hi/lo split of the FP32 weights (|W_b + W_r| =
-// |W_b| + sign(W_b) W_r, since |W_r| <= 2^-8 |W_b|) and every operand value
+// |W_b| + sign(W_b) W_r, since |W_r| <= 2^-8 |W_b|), and every operand value
 // rides as a BF16 hi/lo pair, so each product keeps about 16 significant bits
-// before the FP32 sums. The weights stream from L2 by TMA in 32 KB stages of
-// (128-row tile, 64-wide K slice) pairs through a four-stage ring, running
-// ahead across layers and march steps. The positional encoding, the first
-// layer, the activation rules (App. A), the output layer and the march state
-// run on the SIMT cores in FP32. Plain arithmetic: no rounding radius.
+// before the FP32 sums. Layer 0 takes the encoded input rows (K padded to 64).
+//
+// The weights stream from L2 by TMA as 16 KB tiles (128 rows x 64 K of one
+// matrix) through a ring that runs ahead across layers and march steps. One
+// thread issues the copies (it refills a stage once the MMAs that read it
+// have completed), another issues the MMAs (one tile = 4 MMAs of K = 16),
+// and the whole CTA then runs the epilogue: per neuron and ray, the range,
+// the activation rule (App. A) and the operand rows of the next layer. The
+// encoding, the output layer and the march state run on the SIMT cores in
+// FP32. Plain arithmetic: no rounding radius.
 //
 // Every wait is bounded; a wait that runs out sets the status word, the CTA
-// drains the copies it started (bounded again), frees TMEM and exits.
+// drains the copies and MMAs it started (bounded again), frees TMEM and exits.
 #include <cuda_bf16.h>
 
 #include "sra_common.cuh"
@@ -29,15 +35,15 @@
 namespace sra {
 namespace tcr {
 
-constexpr int NR = 8;       // ray slots per CTA
-constexpr int NCOL = 48;    // operand rows of D: 6 per ray
-constexpr int NXI = 16;     // operand rows of Dx: 2 per ray
-constexpr int MAXDIN = 64;  // network input width (3 + 6 * octaves) bound
-constexpr int NSTG = 4;     // weight ring stages
-constexpr int LA = NSTG - 1;
+constexpr int NR = 16;      // ray slots per CTA
+constexpr int NCOL = 96;    // operand rows of D: 6 per ray
+constexpr int NXI = 32;     // operand rows of Dx: 2 per ray
+constexpr int MAXDIN = 64;  // input width (3 + 6 * octaves) bound: layer 0 has one K slice
+constexpr int TILE = 128 * 128;
+constexpr int kSmemCap = 232448;
 constexpr uint32_t kSpin = 1u << 22;
-enum { C_HI = 0, C_LO = 8, P_HI = 16, P_LO = 24, A_HI = 32, A_LO = 40 };
-enum { X_HI = 0, X_LO = 8 };
+enum { C_HI = 0, C_LO = 16, P_HI = 32, P_LO = 48, A_HI = 64, A_LO = 80 };
+enum { X_HI = 0, X_LO = 16 };
 
 struct RaySlot {
     long long idx;
@@ -45,28 +51,30 @@ struct RaySlot {
     int f0pos, iters, live, pad;
 };
 
+constexpr int align1k(int x) { return (x + 1023) & ~1023; }
+
 template <int H> struct RL {
     static constexpr int MT = H / 128, S = H / 64;
-    static constexpr int TILE = 128 * 128;                // one 128 x 64 BF16 tile
-    static constexpr int STAGE = 2 * TILE;                // a pair of tiles
-    static constexpr int UNITS = 2 * S * MT;              // stages per hidden layer
-    static constexpr int W_OFF = 0;
-    static constexpr int XB_OFF = NSTG * STAGE;
-    static constexpr int XB_SLICE = NCOL * 128;
+    static constexpr int XB_SLICE = NCOL * 128, XI_SLICE = NXI * 128;
+    static constexpr int XB_OFF = 0;
     static constexpr int XI_OFF = XB_OFF + S * XB_SLICE;
-    static constexpr int XI_SLICE = NXI * 128;
-    static constexpr int PE_OFF = XI_OFF + S * XI_SLICE;  // pe[MAXDIN][NR] float4 (c, A, x_inf, p)
-    static constexpr int INP_OFF = PE_OFF + MAXDIN * NR * 16;  // segment inputs [NR][12]
-    static constexpr int NPART = H / 32;
-    static constexpr int OUTP_OFF = INP_OFF + NR * 12 * 4;     // output partial sums [4 NR][NPART]
+    static constexpr int INP_OFF = XI_OFF + S * XI_SLICE;       // segment inputs [NR][12]
+    static constexpr int NPART = H / 64;
+    static constexpr int OUTP_OFF = INP_OFF + NR * 12 * 4;       // output partial sums [4 NR][NPART]
     static constexpr int WOUT_OFF = OUTP_OFF + 4 * NR * NPART * 4;
     static constexpr int RAY_OFF = WOUT_OFF + H * 4;
     static constexpr int BAR_OFF = RAY_OFF + NR * (int)sizeof(RaySlot);
-    static constexpr int MISC_OFF = BAR_OFF + 128;
-    static constexpr int BYTES = MISC_OFF + 64;
-    static constexpr int ALLOC = BYTES + 1024;
-    static_assert(XB_OFF % 1024 == 0 && XB_SLICE % 1024 == 0 && XI_SLICE % 1024 == 0, "operand alignment");
-    static_assert(ALLOC <= 232448, "shared memory");
+    static constexpr int MISC_OFF = BAR_OFF + 256;
+    static constexpr int RING_OFF = align1k(MISC_OFF + 64);
+    static constexpr int NSTG_FIT = (kSmemCap - 1024 - RING_OFF) / TILE;
+    static constexpr int NSTG = NSTG_FIT >= 8 ? 8 : 4;  // 4 measured faster than 5 at H = 512
+    static constexpr int ALLOC = RING_OFF + NSTG * TILE + 1024;
+    static constexpr int TCOLS = MT * 128;                       // TMEM: D (96) + Dx (32) per M-tile
+    static_assert(NSTG_FIT >= 4, "weight ring");
+    static_assert(MT == 1 || MT == 2 || MT == 4, "M tiles");
+    static_assert(2 * NSTG + 2 <= 32, "barrier slots");
+    static_assert(ALLOC <= kSmemCap, "shared memory");
+    static_assert(XI_OFF % 1024 == 0 && XB_SLICE % 1024 == 0 && XI_SLICE % 1024 == 0, "operand alignment");
 };
 
 __device__ __forceinline__ void put_pair(unsigned char *slice, int row_hi, int row_lo, uint32_t kk, float v) {
@@ -81,13 +89,13 @@ __device__ __forceinline__ float get_pair(const unsigned char *slice, int row_hi
            __bfloat162float(*(const __nv_bfloat16 *)(slice + ptx::sw128_offset((uint32_t)row_lo, kk)));
 }
 
-// Operand rows of neuron i (the next layer's K index) for ray slot r.
+// Operand rows at K index k (the next layer's input k) for ray slot r.
 template <int H>
-__device__ __forceinline__ void write_rows(unsigned char *sm, int i, int r, float c, float A, float xi, float p) {
+__device__ __forceinline__ void write_rows(unsigned char *sm, int k, int r, float c, float A, float xi, float p) {
     using L = RL<H>;
-    const uint32_t kk = (uint32_t)(i & 63);
-    unsigned char *xb = sm + L::XB_OFF + (i >> 6) * L::XB_SLICE;
-    unsigned char *xs = sm + L::XI_OFF + (i >> 6) * L::XI_SLICE;
+    const uint32_t kk = (uint32_t)(k & 63);
+    unsigned char *xb = sm + L::XB_OFF + (k >> 6) * L::XB_SLICE;
+    unsigned char *xs = sm + L::XI_OFF + (k >> 6) * L::XI_SLICE;
     put_pair(xb, C_HI + r, C_LO + r, kk, c);
     put_pair(xb, P_HI + r, P_LO + r, kk, p);
     put_pair(xb, A_HI + r, A_LO + r, kk, A);
@@ -108,28 +116,71 @@ __device__ __forceinline__ void activate(int act, int slope, float &c, float &A,
     p = act_eval<float>(act, p);
 }
 
-struct Ring {  // producer / MMA state, held by thread 0
-    uint32_t ld_next, mma_next;
+// A ring unit: one 128 x 64 tile (M tile m, K slice s) of one of the four
+// matrices of linear layer `layer`. Within a layer the units run K slice by
+// K slice, M tile by M tile, matrix by matrix (W_b, W_r, |W_b|, sign W_r).
+struct Unit {
+    int layer, s, m, which;
 };
 
-// Issue the TMA copies of ring unit gi into stage gi % NSTG once the MMAs of
-// that stage's previous use have completed.
+template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
+    using L = RL<H>;
+    Unit r;
+    r.layer = layer;
+    r.which = u & 3;
+    const int ms = u >> 2;
+    r.m = ms & (L::MT - 1);
+    r.s = ms / L::MT;
+    return r;
+}
+
+template <int H> __device__ __forceinline__ int units_of(int layer) {
+    using L = RL<H>;
+    return layer == 0 ? 4 * L::MT : 4 * L::MT * L::S;
+}
+
+// A position in the weight ring: its stage and the parity of that stage's
+// current use (advanced one unit at a time; no division).
+struct RingPos {
+    int st;
+    uint32_t ph;
+};
+
+template <int H> __device__ __forceinline__ void advance(RingPos &r) {
+    if (++r.st == RL<H>::NSTG) {
+        r.st = 0;
+        r.ph ^= 1u;
+    }
+}
+
+// The producer's position in the periodic unit sequence (layer 0, then the
+// hidden layers, then layer 0 of the next march step, ...).
+struct Cursor {
+    uint32_t issued;  // units copied so far (compared modulo 2^32)
+    RingPos pos;
+    int layer, u;
+};
+
+// Issue the copy of the cursor's unit into its stage once the MMAs of that
+// stage's previous use have completed; advance the cursor.
 template <int H>
 __device__ __forceinline__ bool ring_load(unsigned char *sm, uint64_t *bars, const TcRayParams &p, int NL,
-                                          uint32_t gi) {
+                                          Cursor &c) {
     using L = RL<H>;
-    const uint32_t st = gi % NSTG, use = gi / NSTG;
-    if (!ptx::mbar_wait(&bars[NSTG + st], (use & 1u) ^ 1u, kSpin)) return false;
-    const uint32_t u = gi % L::UNITS;
-    const int layer = (int)((gi / L::UNITS) % (uint32_t)NL);
-    const int pair = (int)(u & 1u), ms = (int)(u >> 1);
-    const int s = ms / L::MT, m = ms % L::MT;
-    const CUtensorMap *m0 = pair ? &p.wa[layer] : &p.wb[layer];
-    const CUtensorMap *m1 = pair ? &p.ws[layer] : &p.wr[layer];
-    unsigned char *base = sm + L::W_OFF + st * L::STAGE;
-    ptx::mbar_arrive_expect_tx(&bars[st], L::STAGE);
-    ptx::tma_load_2d(base, m0, s * 64, m * 128, &bars[st]);
-    ptx::tma_load_2d(base + L::TILE, m1, s * 64, m * 128, &bars[st]);
+    const int st = c.pos.st;
+    if (!ptx::mbar_wait(&bars[L::NSTG + st], c.pos.ph ^ 1u, kSpin)) return false;
+    const Unit u = unit_of<H>(c.layer, c.u);
+    const TcLayerMaps &mp = u.layer == 0 ? p.first : p.hidden[u.layer - 1];
+    const CUtensorMap *map = u.which == 0 ? &mp.wb : (u.which == 1 ? &mp.wr : (u.which == 2 ? &mp.wa : &mp.ws));
+    unsigned char *dst = sm + L::RING_OFF + st * TILE;
+    ptx::mbar_arrive_expect_tx(&bars[st], TILE);
+    ptx::tma_load_2d(dst, map, u.s * 64, u.m * 128, &bars[st]);
+    ++c.issued;
+    advance<H>(c.pos);
+    if (++c.u == units_of<H>(c.layer)) {
+        c.u = 0;
+        c.layer = (c.layer == NL) ? 0 : c.layer + 1;
+    }
     return true;
 }
 
@@ -138,42 +189,47 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
     using L = RL<H>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int tid = threadIdx.x, warp = tid >> 5, i = tid;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, i = tid;
     // bars: [0, NSTG) stage full, [NSTG, 2 NSTG) stage empty, then layer done, drain
     uint64_t *bars = (uint64_t *)(sm + L::BAR_OFF);
-    uint64_t *acc_bar = &bars[2 * NSTG], *drain_bar = &bars[2 * NSTG + 1];
+    uint64_t *acc_bar = &bars[2 * L::NSTG], *drain_bar = &bars[2 * L::NSTG + 1];
     uint32_t *tmem_slot = (uint32_t *)(sm + L::MISC_OFF);
     int *abort_flag = (int *)(sm + L::MISC_OFF + 4);
+    uint32_t *consumed = (uint32_t *)(sm + L::MISC_OFF + 8);      // units whose MMAs were issued
+    RingPos *issue_pos = (RingPos *)(sm + L::MISC_OFF + 16);      // the MMA thread's ring position
     RaySlot *slots = (RaySlot *)(sm + L::RAY_OFF);
-    float4 *pe = (float4 *)(sm + L::PE_OFF);
     float *inp = (float *)(sm + L::INP_OFF);
     float *outp = (float *)(sm + L::OUTP_OFF);
     float *wout = (float *)(sm + L::WOUT_OFF);
     const int NL = p.L - 2;  // hidden H -> H layers
     if (tid == 0) {
-        for (int k = 0; k < 2 * NSTG + 2; ++k) ptx::mbar_init(&bars[k], 1);
+        for (int k = 0; k < 2 * L::NSTG + 2; ++k) ptx::mbar_init(&bars[k], 1);
         ptx::fence_mbar_init();
         *abort_flag = 0;
+        *consumed = 0u;
+        issue_pos->st = 0;
+        issue_pos->ph = 0u;
     }
     if (tid < NR) {
         slots[tid].idx = -1;
         slots[tid].live = 0;
     }
-    for (int e = tid; e < (L::S * (L::XB_SLICE + L::XI_SLICE)) / 4; e += H)
-        ((uint32_t *)(sm + L::XB_OFF))[e] = 0u;
     wout[tid] = p.wout[tid];
-    if (warp == 0) ptx::tmem_alloc(tmem_slot, 256);
+    if (warp == 0) ptx::tmem_alloc(tmem_slot, L::TCOLS);
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int m_of = i >> 7;
-    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(m_of * 64);
-    Ring ring = {0u, 0u};
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(m_of * 128);
+    uint32_t gbase = 0;                 // units before the current layer
+    Cursor cur = {0u, {0, 0u}, 0, 0};   // producer thread: next unit to copy
+    RingPos ipos = {0, 0u};             // MMA thread: next unit to consume
     uint32_t accn = 0;
     auto fail = [&](int code) {
         *abort_flag = 1;
         atomicExch(p.status, code);
     };
+    const bool producer = (warp == 0 && lane == 0), issuer = (warp == 1 && lane == 0);
 
     for (;;) {
         // ---- ray slots: refill, then the segment and point of this step -------
@@ -208,127 +264,112 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
         }
         const bool any = __syncthreads_or(tid < NR && slots[tid].live);
         if (!any || *abort_flag) break;
-        // ---- input rows and positional encoding: sin(pi t), cos(pi t), t = 2^k x
-        if (i < p.din) {
-            int d = i, k = -1;
-            bool is_cos = false;
-            if (i >= 3) {
-                const int q = i - 3;
-                k = q / 6;
-                is_cos = (q % 6) >= 3;
-                d = q % 3;
-            }
-            for (int r = 0; r < NR; ++r) {
+        // ---- layer-0 operand rows: the input and its encoding, sin(pi t), cos(pi t), t = 2^k x
+        for (int w = tid; w < MAXDIN * NR; w += H) {
+            const int j = w & (MAXDIN - 1), r = w / MAXDIN;
+            float c = 0.f, A = 0.f, xi = 0.f, pt = 0.f;
+            if (j < p.din) {
                 const float *in = inp + r * 12;
-                if (k < 0) {
-                    pe[i * NR + r] = make_float4(in[d], in[3 + d], 0.f, in[6 + d]);
+                if (j < 3) {
+                    c = in[j];
+                    A = in[3 + j];
+                    pt = in[6 + j];
                 } else {
-                    const float sc = (float)(1 << k), sh = is_cos ? 0.5f : 0.f;
+                    const int q = j - 3, k = q / 6, d = q % 3;
+                    const float sc = (float)(1 << k), sh = ((q % 6) >= 3) ? 0.5f : 0.f;
                     const float ct = sc * in[d] + sh, at = sc * in[3 + d];
                     const float rad = fabsf(at);
                     float a, b, gm;
                     linearize_sinpi<float>(ct - rad, ct + rad, a, b, gm);
-                    pe[i * NR + r] = make_float4(a * ct + b, at * a, fabsf(gm), sinpi_t(sc * in[6 + d] + sh));
+                    c = a * ct + b;
+                    A = at * a;
+                    xi = fabsf(gm);
+                    pt = sinpi_t(sc * in[6 + d] + sh);
                 }
             }
+            write_rows<H>(sm, j, r, c, A, xi, pt);  // zero rows past din
         }
-        __syncthreads();
-        // ---- first layer (din -> H) on the SIMT cores -------------------------
-        {
-            float ac[NR], aa[NR], ax[NR], ap[NR];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) ac[r] = aa[r] = ax[r] = ap[r] = 0.f;
-            for (int j = 0; j < p.din; ++j) {
-                const float w = __ldg(p.W0t + (size_t)j * H + i), aw = fabsf(w);
-#pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const float4 v = pe[j * NR + r];
-                    ac[r] = fmaf(w, v.x, ac[r]);
-                    aa[r] = fmaf(w, v.y, aa[r]);
-                    ax[r] = fmaf(aw, v.z, ax[r]);
-                    ap[r] = fmaf(w, v.w, ap[r]);
-                }
-            }
-            const float b0 = __ldg(p.b[0] + i);
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                float c = ac[r] + b0, A = aa[r], xi = ax[r], pp = ap[r] + b0;
-                activate(p.act[0], p.slope, c, A, xi, pp);
-                write_rows<H>(sm, i, r, c, A, xi, pp);
-            }
-        }
-        // ---- hidden layers on the tensor cores ----------------------------------
-        for (int l = 1; l <= NL; ++l) {
+        // ---- every layer but the output one on the tensor cores --------------
+        for (int l = 0; l <= NL; ++l) {
+            const uint32_t U = (uint32_t)units_of<H>(l);
             ptx::fence_proxy_async();  // operand writes -> async proxy
             ptx::tc_fence_before();    // TMEM reads of the previous layer are done
             __syncthreads();
             if (*abort_flag) break;
-            if (tid == 0) {
+            if (producer) {
                 bool ok = true;
-                while (ok && ring.ld_next < ring.mma_next + LA) {
-                    ok = ring_load<H>(sm, bars, p, NL, ring.ld_next);
-                    if (ok) ++ring.ld_next;
-                }
-                const uint32_t id = ptx::idesc_bf16(128, NCOL), ix = ptx::idesc_bf16(128, NXI);
-                for (int u = 0; u < L::UNITS && ok; ++u) {
-                    const uint32_t gi = ring.mma_next, st = gi % NSTG;
-                    if (!ptx::mbar_wait(&bars[st], (gi / NSTG) & 1u, kSpin)) { ok = false; break; }
-                    ptx::tc_fence_after();
-                    const int pair = u & 1, ms = u >> 1, s = ms / L::MT, m = ms % L::MT;
-                    unsigned char *base = sm + L::W_OFF + st * L::STAGE;
-                    const uint32_t b_addr = pair ? ptx::smem_u32(sm + L::XI_OFF + s * L::XI_SLICE)
-                                                 : ptx::smem_u32(sm + L::XB_OFF + s * L::XB_SLICE);
-                    const uint32_t d_col = tmem + (uint32_t)(m * 64 + (pair ? NCOL : 0));
-                    const uint32_t idesc = pair ? ix : id;
-#pragma unroll
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint64_t bd = ptx::desc_kmajor_sw128(b_addr) + 2 * ks;
-                        const uint64_t a0 = ptx::desc_kmajor_sw128(ptx::smem_u32(base)) + 2 * ks;
-                        const uint64_t a1 = ptx::desc_kmajor_sw128(ptx::smem_u32(base + L::TILE)) + 2 * ks;
-                        ptx::mma_bf16(d_col, a0, bd, idesc, (s | ks) ? 1u : 0u);
-                        ptx::mma_bf16(d_col, a1, bd, idesc, 1u);
-                    }
-                    ptx::mma_commit(&bars[NSTG + st]);
-                    if (u + 1 == L::UNITS) ptx::mma_commit(acc_bar);
-                    ++ring.mma_next;
-                    while (ok && ring.ld_next < ring.mma_next + LA) {
-                        ok = ring_load<H>(sm, bars, p, NL, ring.ld_next);
-                        if (ok) ++ring.ld_next;
-                    }
-                }
+                // copies run up to NSTG - 1 units past this layer's end
+                while (ok && (int32_t)(cur.issued - (gbase + U + (L::NSTG - 1))) < 0)
+                    ok = ring_load<H>(sm, bars, p, NL, cur);
                 if (!ok) fail(6);
+            } else if (issuer) {
+                bool ok = true;
+                const uint32_t iD = ptx::idesc_bf16(128, NCOL), iX = ptx::idesc_bf16(128, NXI);
+                for (uint32_t k = 0; k < U && ok; ++k) {
+                    const int st = ipos.st;
+                    if (!ptx::mbar_wait(&bars[st], ipos.ph, kSpin)) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const Unit u = unit_of<H>(l, (int)k);
+                    const bool dx = u.which >= 2;
+                    const uint32_t b_addr = dx ? ptx::smem_u32(sm + L::XI_OFF + u.s * L::XI_SLICE)
+                                               : ptx::smem_u32(sm + L::XB_OFF + u.s * L::XB_SLICE);
+                    const uint32_t d_col = tmem + (uint32_t)(u.m * 128 + (dx ? NCOL : 0));
+                    const uint32_t idesc = dx ? iX : iD;
+                    const bool first = (u.which & 1) == 0 && u.s == 0;
+                    const uint64_t a0 = ptx::desc_kmajor_sw128(ptx::smem_u32(sm + L::RING_OFF + st * TILE));
+                    const uint64_t b0 = ptx::desc_kmajor_sw128(b_addr);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        ptx::mma_bf16(d_col, a0 + 2 * ks, b0 + 2 * ks, idesc, (first && ks == 0) ? 0u : 1u);
+                    ptx::mma_commit(&bars[L::NSTG + st]);
+                    if (k + 1 == U) ptx::mma_commit(acc_bar);
+                    advance<H>(ipos);
+                }
+                *consumed += U;  // published once per layer for the exit drain
+                *issue_pos = ipos;
+                if (!ok) fail(7);
             }
-            __syncthreads();
-            if (*abort_flag) break;
-            if (!ptx::mbar_wait(acc_bar, accn & 1u, kSpin)) fail(7);
+            __syncwarp();
+            gbase += U;
+            if (!ptx::mbar_wait(acc_bar, accn & 1u, kSpin)) fail(8);
             accn++;
             ptx::tc_fence_after();
             __syncthreads();
             if (*abort_flag) break;
-            // epilogue: neuron i of every ray slot; the layer's operands are free
-            float v[64];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) ptx::tmem_ld16(tl + q * 16, v + q * 16);
-            ptx::tmem_wait_ld();
+            // epilogue: neuron i of every ray slot (the layer's operands are free)
             const float bias = __ldg(p.b[l] + i);
             const int act = p.act[l];
+#pragma unroll 1
+            for (int g = 0; g < NR / 8; ++g) {
+                float v[64];
+                const int r0 = g * 8;
+                ptx::tmem_ld8(tl + C_HI + r0, v + 0);
+                ptx::tmem_ld8(tl + C_LO + r0, v + 8);
+                ptx::tmem_ld8(tl + P_HI + r0, v + 16);
+                ptx::tmem_ld8(tl + P_LO + r0, v + 24);
+                ptx::tmem_ld8(tl + A_HI + r0, v + 32);
+                ptx::tmem_ld8(tl + A_LO + r0, v + 40);
+                ptx::tmem_ld8(tl + NCOL + X_HI + r0, v + 48);
+                ptx::tmem_ld8(tl + NCOL + X_LO + r0, v + 56);
+                ptx::tmem_wait_ld();
 #pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                float c = (v[C_HI + r] + v[C_LO + r]) + bias;
-                float pp = (v[P_HI + r] + v[P_LO + r]) + bias;
-                float A = v[A_HI + r] + v[A_LO + r];
-                float xi = v[NCOL + X_HI + r] + v[NCOL + X_LO + r];
-                activate(act, p.slope, c, A, xi, pp);
-                write_rows<H>(sm, i, r, c, A, xi, pp);
+                for (int r = 0; r < 8; ++r) {
+                    float c = (v[r] + v[8 + r]) + bias;
+                    float pp = (v[16 + r] + v[24 + r]) + bias;
+                    float A = v[32 + r] + v[40 + r];
+                    float xi = v[48 + r] + v[56 + r];
+                    activate(act, p.slope, c, A, xi, pp);
+                    write_rows<H>(sm, i, r0 + r, c, A, xi, pp);
+                }
             }
         }
         __syncthreads();
         if (*abort_flag) break;
-        // ---- output layer (H -> 1): 4 sums per ray, H/32 parts of 32 inputs each
+        // ---- output layer (H -> 1): 4 sums per ray, H/64 parts of 64 inputs each
         {
-            const int q = tid & 31, part = tid >> 5, r = q >> 2, kind = q & 3;
+            const int q = tid & 63, part = tid >> 6, r = q >> 2, kind = q & 3;
             float acc = 0.f;
-            for (int j = part * 32; j < part * 32 + 32; ++j) {
+            for (int j = part * 64; j < part * 64 + 64; ++j) {
                 const uint32_t kk = (uint32_t)(j & 63);
                 const unsigned char *xb = sm + L::XB_OFF + (j >> 6) * L::XB_SLICE;
                 const unsigned char *xs = sm + L::XI_OFF + (j >> 6) * L::XI_SLICE;
@@ -374,21 +415,28 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
         }
         __syncthreads();
     }
-    // drain: the copies still in flight land before the CTA exits, and every
-    // MMA issued (also after an abort) completes before TMEM is freed
-    if (tid == 0) {
-        for (uint32_t gi = ring.mma_next; gi < ring.ld_next; ++gi)
-            if (!ptx::mbar_wait(&bars[gi % NSTG], (gi / NSTG) & 1u, kSpin)) {
-                atomicExch(p.status, 8);
-                break;
-            }
+    // drain: every issued MMA completes and every copy in flight lands before
+    // TMEM is freed and the CTA exits
+    __syncthreads();
+    if (issuer) {
         ptx::mma_commit(drain_bar);
         if (!ptx::mbar_wait(drain_bar, 0u, kSpin)) atomicExch(p.status, 9);
     }
+    if (producer) {  // the copies issued but never consumed, from the MMA thread's position on
+        RingPos r = *issue_pos;
+        for (uint32_t gi = *consumed; (int32_t)(gi - cur.issued) < 0; ++gi) {
+            if (!ptx::mbar_wait(&bars[r.st], r.ph, kSpin)) {
+                atomicExch(p.status, 10);
+                break;
+            }
+            advance<H>(r);
+        }
+    }
+    __syncwarp();
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 0) ptx::tmem_dealloc(tmem, 256);
+    if (warp == 0) ptx::tmem_dealloc(tmem, L::TCOLS);
 }
 
 }  // namespace tcr
@@ -398,6 +446,8 @@ int tc_ray_smem_bytes(int H) {
 }
 
 int tc_ray_max_din() { return tcr::MAXDIN; }
+
+int tc_ray_slots() { return tcr::NR; }
 
 template <int H> static cudaError_t launch_r(const TcRayParams &p, int grid, cudaStream_t st) {
     const int smem = tc_ray_smem_bytes(H);

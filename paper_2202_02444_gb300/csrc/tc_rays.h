@@ -1,4 +1,4 @@
-// Parameters of the tensor-core CastRay kernel (BF16 hidden layers).
+// Parameters of the tensor-core CastRay kernel (BF16 layers on tcgen05).
 #pragma once
 
 #include <cuda.h>
@@ -10,15 +10,19 @@ namespace sra {
 
 constexpr int kMaxRayTc = 8;  // hidden H -> H layers served by the tensor cores
 
+// One linear layer as four BF16 matrices, row-major [H][K] (K-major tiles):
+// W_b = bf16(W), W_r = bf16(W - W_b), |W_b|, and sign(W_b) W_r, so that
+// W_b + W_r ~ W and |W_b| + sign(W_b) W_r = |W_b + W_r| (|W_r| <= 2^-8 |W_b|).
+struct TcLayerMaps {
+    CUtensorMap wb, wr, wa, ws;
+};
+
 struct TcRayParams {
-    CUtensorMap wb[kMaxRayTc];  // W_b = bf16(W)                 [H][H] row-major
-    CUtensorMap wr[kMaxRayTc];  // W_r = bf16(W - W_b)
-    CUtensorMap wa[kMaxRayTc];  // |W_b|
-    CUtensorMap ws[kMaxRayTc];  // sign(W_b) W_r, so |W_b| + sign(W_b) W_r = |W_b + W_r|
-    const float *W0t;           // first layer, transposed [din][H] (FP32)
+    TcLayerMaps first;              // layer 0, K padded to 64 with zero columns
+    TcLayerMaps hidden[kMaxRayTc];  // H -> H layers
     const float *b[kMaxRayTc + 2];
-    int act[kMaxRayTc + 1];     // activation after linear layer l
-    const float *wout;          // output layer [H]
+    int act[kMaxRayTc + 1];  // activation after linear layer l
+    const float *wout;       // output layer [H]
     float bout;
     int L, din, pe, slope;
     int *status;
@@ -34,6 +38,7 @@ struct TcRayParams {
 
 int tc_ray_smem_bytes(int H);
 int tc_ray_max_din();
+int tc_ray_slots();  // rays per CTA
 cudaError_t launch_tc_rays(int H, const TcRayParams &p, int grid, cudaStream_t st);
 
 }  // namespace sra
