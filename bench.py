@@ -540,25 +540,50 @@ def main():
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
     agree[fin] &= np.abs(ta[fin] - tb[fin]) <= 1e-4 * 1.0001 + 1e-6
 
-    # mesh phase: marching tetrahedra in level-7 octree cells of the 256x8 net,
-    # 2^3 cells per leaf axis (1024^3 effective resolution, the meshing step
-    # the level-10 octree of this network feeds)
+    # mesh phase: hierarchical mesh extraction (Sec. 4.7) of the ReLU
+    # 3-32-32-1 network (the 256x8 network is negative everywhere in the root
+    # box: it has no surface): UNKNOWN leaves at depth 7, then 8^3 sub-cells per
+    # leaf (1024^3 effective grid), marching tetrahedra
     mesh = None
     if rank == 0:
-        nl = min(16384, B)
-        ml = fr[:nl].contiguous()
-        sra.mesh_leaves(net_box, ml[:64], 3)
+        net_small = sra.Net(wl.net_small_relu())
+        mo = sra.make_opts(arith="fixed")
+        sra.mesh_leaves(net_small, sra.extract_leaves(net_small, 3, opts=mo)[0], 3)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tris = sra.mesh_leaves(net_box, ml, 3)
+        ml, _ = sra.extract_leaves(net_small, 7, opts=mo)
         torch.cuda.synchronize()
-        mt = time.perf_counter() - t0
-        mesh = {"workload": f"{nl} level-7 frontier cells of ReLU 3-[256]x8-1, 8^3 sub-cells each "
-                            "(1024^3 effective grid), marching tetrahedra",
-                "leaves": nl, "triangles": int(tris.shape[0]), "s": mt,
-                "leaves_per_s": nl / mt, "point_evals_per_s": nl * 729 / mt,
-                "timing": "host clock around one synchronous sra_mesh_leaves call"}
+        t1 = time.perf_counter()
+        tris = sra.mesh_leaves(net_small, ml, 3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        nl = int(ml.shape[0])
+        mesh = {"workload": "ReLU 3-32-32-1 (seed 0): UNKNOWN leaves of its depth-7 octree (affine-fixed), "
+                            "8^3 sub-cells per leaf (1024^3 effective grid), marching tetrahedra",
+                "leaves": nl, "leaf_fraction": nl / 8 ** 7, "triangles": int(tris.shape[0]),
+                "tree_s": t1 - t0, "mesh_s": t2 - t1, "leaves_per_s": nl / (t2 - t1),
+                "point_evals_per_s": nl * 729 / (t2 - t1),
+                "timing": "host clock around the synchronous calls"}
         del tris
+        net_small.close()
+
+    # empty-sphere queries (Sec. 4.4) on the same network
+    spheres = None
+    if rank == 0:
+        qp = torch.from_numpy(np.random.default_rng(9).uniform(-1, 1, (1 << 16, 3)).astype(np.float32)).to(dev)
+        so = sra.make_opts(arith="truncate", K=K)
+        sra.empty_spheres(net_box, qp[:256], 1.0, 12, opts=so)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rad = sra.empty_spheres(net_box, qp, 1.0, 12, opts=so)
+        e1.record()
+        torch.cuda.synchronize()
+        sms = e0.elapsed_time(e1)
+        spheres = {"workload": "65,536 uniform points in [-1,1]^3, ReLU 3-[256]x8-1, affine-truncate K=64 FP32, "
+                               "boxes of half-width 2^-k, k < 12",
+                   "ms": sms, "queries_per_s": (1 << 16) / (sms / 1e3),
+                   "decided_frac": float((rad > 0).float().mean()), "median_radius": float(rad.median())}
 
     batched = None
     if not args.no_batched and rank == 0:
@@ -623,6 +648,7 @@ def main():
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
                      / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
             "mesh": mesh,
+            "empty_spheres": spheres,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -269,6 +269,19 @@ sra_status sra_mesh_leaves(const sra_net *net, const float *root_lo, const float
                            const sra_node *leaves, int64_t n_leaves, int32_t sub_levels,
                            float *tris_out, int64_t cap, int64_t *n_tris, void *stream);
 
+/* Empty-sphere queries (Sec. 4.4). For every point p (device float[n][3])
+ * writes radius_out[i] (device float[n]): the largest r = r_max * 2^-k,
+ * 0 <= k < levels, whose box [p - r, p + r] range analysis classifies
+ * POSITIVE or NEGATIVE (Proc. 1 with opts), else 0. The box of half-width r
+ * contains the ball of radius r, so that ball does not meet f = 0. Runs
+ * `levels` rounds over the points still open (no host synchronisation).
+ * Precision FP32 or FP64; opts->recheck re-bounds near-zero FP32 results in
+ * FP64. Uses stream-ordered scratch of about 30 bytes per point. Errors:
+ * SRA_EINVAL (r_max <= 0, levels outside [1, 30], n > 2^31 - 1),
+ * SRA_EUNSUPPORTED (BF16 precisions), SRA_ENOMEM, SRA_ECUDA. Asynchronous. */
+sra_status sra_empty_spheres(const sra_net *net, const sra_opts *opts, const float *points, int64_t n,
+                             float r_max, int32_t levels, float *radius_out, void *stream);
+
 /* Plain forward evaluation f(x) for n points (device float[n][3] -> device
  * float[n]) in the network's FP32 weights. Asynchronous. */
 sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, void *stream);

@@ -234,3 +234,23 @@ def cast_rays(net, origins, dirs, arith="fixed", K=0, slope="chebyshev", delta=1
                         it.ctypes.data_as(C.POINTER(C.c_int64)),
                         st.ctypes.data_as(C.POINTER(C.c_int32)), _dp(mg), int(nthreads))
     return {"t": t, "iters": it, "status": st, "margin": mg}
+
+
+def empty_spheres(net, points, r_max, levels, arith="fixed", K=0, slope="chebyshev"):
+    """Empty-sphere query (Sec. 4.4): for each point p, the largest
+    r = r_max * 2^-k (0 <= k < levels) such that RangeBound (Proc. 1) of the
+    box [p - r, p + r] is POSITIVE or NEGATIVE, else 0. The box contains the
+    ball of radius r around p, which therefore misses the zero set."""
+    points = np.asarray(points, np.float64).reshape(-1, 3)
+    radius = np.zeros(len(points))
+    open_ = np.arange(len(points))
+    r = float(r_max)
+    for _ in range(int(levels)):
+        if len(open_) == 0:
+            break
+        res = bound_boxes(net, points[open_], np.full((len(open_), 3), r), arith, K, slope)
+        done = res["cls"] != UNKNOWN
+        radius[open_[done]] = r
+        open_ = open_[~done]
+        r *= 0.5
+    return radius

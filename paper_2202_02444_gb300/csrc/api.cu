@@ -658,6 +658,52 @@ sra_status sra_eval(const sra_net *n, const float *x, int64_t count, float *y, v
     return run_bound(n, &o, false, 1, src, out, count, as_stream(stream));
 }
 
+sra_status sra_empty_spheres(const sra_net *n, const sra_opts *o, const float *points, int64_t count, float r_max,
+                             int32_t levels, float *radius, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (o->precision != SRA_PREC_FP32 && o->precision != SRA_PREC_FP64)
+        return fail(SRA_EUNSUPPORTED, "empty-sphere queries run in FP32 or FP64");
+    if (!(r_max > 0.f) || levels < 1 || levels > 30) return fail(SRA_EINVAL, "need r_max > 0 and 1 <= levels <= 30");
+    if (count < 0 || count > INT32_MAX) return fail(SRA_EINVAL, "n outside [0, 2^31 - 1]");
+    if (count == 0) return SRA_OK;
+    if (!points || !radius) return fail(SRA_EINVAL, "null points / radius_out");
+    cudaStream_t st = as_stream(stream);
+    const size_t b_list = align16((size_t)count * 4), b_hw = align16((size_t)count * 12), b_cls = align16((size_t)count);
+    Scratch sc;
+    if ((r = scratch_alloc(sc, 2 * b_list + b_hw + b_cls + 64, st))) return r;
+    char *base = (char *)sc.p;
+    int *list[2] = {(int *)base, (int *)(base + b_list)};
+    float *halfw = (float *)(base + 2 * b_list);
+    uint8_t *cls = (uint8_t *)(base + 2 * b_list + b_hw);
+    int *cnt = (int *)(base + 2 * b_list + b_hw + b_cls);  // [0], [1]: list counts; [4..5]: recheck tally
+    cudaError_t e = launch_sphere_init(count, list[0], &cnt[0], radius, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "sphere init: %s", cudaGetErrorString(e));
+    float rk = r_max;
+    for (int k = 0; k < levels; ++k, rk *= 0.5f) {
+        const int a = k & 1, b = a ^ 1;
+        SRA_CK(cudaMemsetAsync(&cnt[b], 0, sizeof(int), st));
+        if ((e = launch_sphere_halfw(count, list[a], &cnt[a], rk, halfw, st)) != cudaSuccess)
+            return fail(SRA_ECUDA, "sphere half-widths: %s", cudaGetErrorString(e));
+        BoxSrc src;
+        memset(&src, 0, sizeof src);
+        src.kind = SRC_BOXES;
+        src.centers = points;
+        src.halfw = halfw;
+        src.list = list[a];
+        src.list_count = &cnt[a];
+        BoundOut out;
+        memset(&out, 0, sizeof out);
+        out.cls = cls;
+        if ((r = bound_with_recheck(n, o, src, out, count, (unsigned long long *)&cnt[4], st))) return r;
+        if ((e = launch_sphere_update(count, list[a], &cnt[a], cls, rk, radius, list[b], &cnt[b], st)) != cudaSuccess)
+            return fail(SRA_ECUDA, "sphere update: %s", cudaGetErrorString(e));
+    }
+    return SRA_OK;
+}
+
 sra_status sra_mesh_leaves(const sra_net *n, const float *root_lo, const float *root_hi, const sra_node *leaves,
                            int64_t n_leaves, int32_t sub_levels, float *tris, int64_t cap, int64_t *n_tris,
                            void *stream) {

@@ -69,6 +69,13 @@ cudaError_t launch_mesh_points(const MeshArgs &a, float *pts, cudaStream_t st);
 cudaError_t launch_mesh_tris(const MeshArgs &a, const float *vals, long long *blk, unsigned long long *counter,
                              float *tris, long long cap, cudaStream_t st);
 
+// Empty-sphere rounds over a device-side list of open points.
+cudaError_t launch_sphere_init(long long n, int *list, int *count, float *radius, cudaStream_t st);
+cudaError_t launch_sphere_halfw(long long n, const int *list, const int *count, float r, float *halfw,
+                                cudaStream_t st);
+cudaError_t launch_sphere_update(long long n, const int *list, const int *count, const uint8_t *cls, float r,
+                                 float *radius, int *next_list, int *next_count, cudaStream_t st);
+
 // counts: device int64[nseg][SRA_CNT_N]; blk: scratch 2 * nblk
 cudaError_t launch_split_batch(const uint8_t *cls, const sra_node *in, const BatchSplitSeg *segs, int nseg,
                                long long nblk, sra_node *out, sra_node *leaves, unsigned long long *counts,

@@ -97,11 +97,12 @@ _lib.sra_classify_and_split_batch.argtypes = [C.POINTER(_vp), C.POINTER(Opts), C
                                               C.POINTER(BatchSeg), C.c_int32, _vp, _vp, _vp, _vp]
 _lib.sra_mesh_leaves.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp, C.c_int64, C.c_int32,
                                  _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
+_lib.sra_empty_spheres.argtypes = [_vp, C.POINTER(Opts), _vp, C.c_int64, C.c_float, C.c_int32, _vp, _vp]
 _lib.sra_serve.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(Opts), C.c_int32,
                            C.POINTER(ServeCfg), C.POINTER(Request), C.c_int64]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
            "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve",
-           "sra_classify_and_split_batch", "sra_mesh_leaves"):
+           "sra_classify_and_split_batch", "sra_mesh_leaves", "sra_empty_spheres"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -285,6 +286,18 @@ def mesh_leaves(net, leaves, sub_levels=3, root_lo=(-1.0, -1.0, -1.0), root_hi=(
         return mesh_leaves(net, leaves, sub_levels, root_lo, root_hi, cap=int(nt.value))
     _check(code)
     return tris[:nt.value]
+
+
+def empty_spheres(net, points, r_max=1.0, levels=12, opts=None, radius=None, **kw):
+    """Empty-sphere radius per point (Sec. 4.4): the largest r_max * 2^-k whose
+    box around the point is proven POSITIVE or NEGATIVE, else 0."""
+    opts = opts or make_opts(**kw)
+    _need(points, torch.float32, 3, "points")
+    n = points.shape[0]
+    radius = radius if radius is not None else torch.empty(n, dtype=torch.float32, device=points.device)
+    _check(_lib.sra_empty_spheres(net.handle, C.byref(opts), _ptr(points), n, float(r_max), int(levels),
+                                  _ptr(radius), _stream()))
+    return radius
 
 
 def cast_rays(net, origins, dirs, opts=None, t_hit=None, iters=None, **kw):
