@@ -238,6 +238,27 @@ sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *
                          const float *dirs, int64_t n, float *t_hit, int32_t *iters,
                          void *stream);
 
+/* Frustum ray casting (Sec. 4.3) for a pinhole image: width x height pixel
+ * rays from one eye (host float[3]) along unit directions dirs (device
+ * float[height * width][3], row-major, the rays of a pinhole camera: each
+ * pixel's direction a positive combination of its rectangle's corner
+ * directions). A grid x grid set of coarse frusta marches like Proc. 2: each
+ * frustum bounds its segment [t, t + sigma] by one box that contains every
+ * pixel ray's points (the truncated pyramid of its corner rays, far face
+ * pushed out by 1 / cos of the widest corner angle), advances on POSITIVE or
+ * NEGATIVE, shrinks sigma on UNKNOWN, splits its longer pixel side when that
+ * side is wider than 2 sigma at the far face, and hands single pixels to the
+ * ray kernel of opts->precision, which resumes Proc. 2 from the frustum's
+ * (t, sigma). Frustum boxes are bounded in FP32 (with opts->recheck, FP64
+ * near zero). Writes t_hit (device float[height * width]: t, +inf for
+ * NO_HIT, NaN at the iteration cap) and, if not NULL, iters (device
+ * int32[height * width]: ray iterations after the hand-over). stats (host
+ * int64[4], may be NULL): frustum rounds, frustum boxes bounded, pixels
+ * handed to rays, 0. Synchronises once per round. Errors as sra_cast_rays. */
+sra_status sra_cast_frustum(const sra_net *net, const sra_opts *opts, const float *eye, const float *dirs,
+                            int32_t width, int32_t height, int32_t grid, float *t_hit, int32_t *iters,
+                            int64_t *stats, void *stream);
+
 /* Proc. 3 to a fixed depth from the root box [xl, xu] (host float[3]): runs
  * sra_classify_and_split level by level and writes the UNKNOWN nodes at
  * `depth` to leaves_out (device sra_node[cap]) in level-order; these are the

@@ -974,10 +974,11 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     return SRA_OK;
 }
 
-sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origins,
-                         const float *dirs, int64_t count, float *t_hit, int32_t *iters,
-                         void *stream) {
-    g_err.clear();
+// Proc. 2 for `count` rays, resuming each ray from (t_start[i], sigma_start[i])
+// when those are given (the hand-over of frustum casting).
+static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const float *origins, const float *dirs,
+                                 int64_t count, float *t_hit, int32_t *iters, const float *t_start,
+                                 const float *sigma_start, void *stream) {
     sra_status r = check_net(n);
     if (r) return r;
     if ((r = check_opts(o))) return r;
@@ -1013,6 +1014,8 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
         p.f0 = f0;
         p.t_hit = t_hit;
         p.iters = iters;
+        p.t_start = t_start;
+        p.sigma_start = sigma_start;
         p.n = count;
         p.next = next;
         p.delta = o->delta;
@@ -1040,6 +1043,8 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
     rp.f0 = f0;
     rp.t_hit = t_hit;
     rp.iters = iters;
+    rp.t_start = t_start;
+    rp.sigma_start = sigma_start;
     rp.n = count;
     rp.next = next;
     rp.delta = o->delta;
@@ -1056,6 +1061,113 @@ sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origi
     cudaError_t e = launch_rays_f32(kmax, n->dev, &rp, cfg, (int)grid, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "ray kernel launch: %s", cudaGetErrorString(e));
     return SRA_OK;
+}
+
+sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *eye, const float *dirs, int32_t W,
+                            int32_t Hh, int32_t grid, float *t_hit, int32_t *iters, int64_t *stats, void *stream) {
+    g_err.clear();
+    sra_status r = check_net(n);
+    if (r) return r;
+    if ((r = check_opts(o))) return r;
+    if (!eye || !dirs || !t_hit) return fail(SRA_EINVAL, "null eye / dirs / t_hit");
+    if (W < 1 || Hh < 1 || (long long)W * Hh > INT32_MAX || grid < 1 || grid > 4096)
+        return fail(SRA_EINVAL, "bad image size %d x %d or grid %d", W, Hh, grid);
+    if (!(o->delta > 0.f) || !(o->t_max > 0.f) || !(o->sigma0 > 0.f) || !(o->eta_plus >= 1.f) ||
+        !(o->eta_minus > 0.f && o->eta_minus < 1.f) || !(o->safety > 0.f && o->safety <= 1.f) || o->max_iters < 1)
+        return fail(SRA_EINVAL, "ray options out of range");
+    if (o->precision != SRA_PREC_FP32 && o->precision != SRA_PREC_BF16)
+        return fail(SRA_EUNSUPPORTED, "frustum casting hands pixels to the FP32 or BF16 ray kernels");
+    cudaStream_t st = as_stream(stream);
+    const long long npix = (long long)W * Hh;
+    FrustumArgs a;
+    memset(&a, 0, sizeof a);
+    a.dirs = dirs;
+    a.W = W;
+    a.H = Hh;
+    for (int d = 0; d < 3; ++d) a.eye[d] = eye[d];
+    a.sigma0 = o->sigma0;
+    a.t_max = o->t_max;
+    a.eta_plus = o->eta_plus;
+    a.eta_minus = o->eta_minus;
+    a.safety = o->safety;
+    a.delta = o->delta;
+    sra_opts bo = *o;  // frustum boxes: FP32 bounds of the same arithmetic
+    bo.precision = SRA_PREC_FP32;
+    const size_t b_fr = align16((size_t)npix * sizeof(Frustum)), b_v3 = align16((size_t)npix * 12),
+                 b_1 = align16((size_t)npix), b_4 = align16((size_t)npix * 4);
+    Scratch sc;
+    if ((r = scratch_alloc(sc, 2 * b_fr + 2 * b_v3 + b_1 + 3 * b_4 + 64, st))) return r;
+    char *p = (char *)sc.p;
+    Frustum *fr[2] = {(Frustum *)p, (Frustum *)(p + b_fr)};
+    p += 2 * b_fr;
+    float *centers = (float *)p, *halfw = (float *)(p + b_v3);
+    p += 2 * b_v3;
+    uint8_t *cls = (uint8_t *)p;
+    p += b_1;
+    int *ray_pix = (int *)p;
+    float *ray_t = (float *)(p + b_4), *ray_sigma = (float *)(p + 2 * b_4);
+    p += 3 * b_4;
+    int *cnt = (int *)p;  // [0] current frusta, [1] next frusta, [2] rays, [4..5] recheck tally
+    SRA_CK(cudaMemsetAsync(cnt, 0, 64, st));
+    cudaError_t e = launch_frustum_init(a, grid, fr[0], &cnt[0], st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "frustum init: %s", cudaGetErrorString(e));
+    const int tw = (W + grid - 1) / grid, th = (Hh + grid - 1) / grid;
+    long long nf = (long long)((W + tw - 1) / tw) * ((Hh + th - 1) / th);
+    long long rounds = 0, boxes = 0;
+    int host_cnt[3] = {0, 0, 0};
+    int cur = 0;
+    while (nf > 0) {
+        if (++rounds > 1000000) return fail(SRA_ETIMEOUT, "frustum march did not finish");
+        SRA_CK(cudaMemsetAsync(&cnt[1], 0, sizeof(int), st));
+        if ((e = launch_frustum_boxes(a, fr[cur], &cnt[0], nf, centers, halfw, st)) != cudaSuccess)
+            return fail(SRA_ECUDA, "frustum boxes: %s", cudaGetErrorString(e));
+        BoxSrc src;
+        memset(&src, 0, sizeof src);
+        src.kind = SRC_BOXES;
+        src.centers = centers;
+        src.halfw = halfw;
+        src.n = nf;
+        BoundOut out;
+        memset(&out, 0, sizeof out);
+        out.cls = cls;
+        if ((r = bound_with_recheck(n, &bo, src, out, nf, (unsigned long long *)&cnt[4], st))) return r;
+        if ((e = launch_frustum_update(a, fr[cur], &cnt[0], nf, cls, fr[cur ^ 1], &cnt[1], ray_pix, ray_t, ray_sigma,
+                                       &cnt[2], t_hit, iters, st)) != cudaSuccess)
+            return fail(SRA_ECUDA, "frustum update: %s", cudaGetErrorString(e));
+        SRA_CK(cudaMemcpyAsync(&cnt[0], &cnt[1], sizeof(int), cudaMemcpyDeviceToDevice, st));
+        SRA_CK(cudaMemcpyAsync(host_cnt, cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        SRA_CK(cudaStreamSynchronize(st));
+        boxes += nf;
+        nf = host_cnt[0];
+        cur ^= 1;
+    }
+    const int nr = host_cnt[2];
+    if (stats) {
+        stats[0] = rounds;
+        stats[1] = boxes;
+        stats[2] = nr;
+        stats[3] = 0;
+    }
+    if (nr == 0) return SRA_OK;
+    Scratch sr;
+    const size_t b_r3 = align16((size_t)nr * 12), b_r = align16((size_t)nr * 4);
+    if ((r = scratch_alloc(sr, 2 * b_r3 + 2 * b_r, st))) return r;
+    float *org = (float *)sr.p, *dr = (float *)((char *)sr.p + b_r3);
+    float *t_ray = (float *)((char *)sr.p + 2 * b_r3);
+    int *it_ray = (int *)((char *)sr.p + 2 * b_r3 + b_r);
+    if ((e = launch_ray_gather(a, ray_pix, nr, org, dr, st)) != cudaSuccess)
+        return fail(SRA_ECUDA, "ray gather: %s", cudaGetErrorString(e));
+    if ((r = cast_rays_impl(n, o, org, dr, nr, t_ray, it_ray, ray_t, ray_sigma, stream))) return r;
+    if ((e = launch_ray_scatter(ray_pix, nr, t_ray, it_ray, t_hit, iters, st)) != cudaSuccess)
+        return fail(SRA_ECUDA, "ray scatter: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
+sra_status sra_cast_rays(const sra_net *n, const sra_opts *o, const float *origins,
+                         const float *dirs, int64_t count, float *t_hit, int32_t *iters,
+                         void *stream) {
+    g_err.clear();
+    return cast_rays_impl(n, o, origins, dirs, count, t_hit, iters, nullptr, nullptr, stream);
 }
 
 sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *xl, const float *xu,

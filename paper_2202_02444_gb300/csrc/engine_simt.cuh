@@ -524,8 +524,8 @@ ray_kernel(NetDev net, RayParams rp, RangeCfg cfg) {
             const unsigned long long q = atomicAdd(rp.next, 1ull);
             if ((long long)q < rp.n) {
                 st->idx = (long long)q;
-                st->t = 0.f;
-                st->sigma = rp.sigma0;
+                st->t = rp.t_start ? rp.t_start[q] : 0.f;
+                st->sigma = rp.sigma_start ? rp.sigma_start[q] : rp.sigma0;
                 st->iters = 0;
                 st->f0pos = rp.f0[q] >= 0.f;
                 st->live = 1;

@@ -76,6 +76,28 @@ cudaError_t launch_sphere_halfw(long long n, const int *list, const int *count, 
 cudaError_t launch_sphere_update(long long n, const int *list, const int *count, const uint8_t *cls, float r,
                                  float *radius, int *next_list, int *next_count, cudaStream_t st);
 
+// Frustum ray casting: frusta over pixel rectangles of one eye.
+struct Frustum {
+    int x0, y0, x1, y1;  // pixels [x0, x1) x [y0, y1)
+    float t, sigma;
+};
+struct FrustumArgs {
+    const float *dirs;  // unit pixel directions [H * W][3], row-major
+    int W, H;
+    float eye[3];
+    float sigma0, t_max, eta_plus, eta_minus, safety, delta;
+};
+cudaError_t launch_frustum_init(const FrustumArgs &a, int grid, Frustum *out, int *count, cudaStream_t st);
+cudaError_t launch_frustum_boxes(const FrustumArgs &a, const Frustum *fr, const int *count, long long n_hint,
+                                 float *centers, float *halfw, cudaStream_t st);
+cudaError_t launch_frustum_update(const FrustumArgs &a, const Frustum *fr, const int *count, long long n_hint,
+                                  const uint8_t *cls, Frustum *out, int *out_count, int *ray_pix, float *ray_t,
+                                  float *ray_sigma, int *ray_count, float *t_hit, int *iters, cudaStream_t st);
+cudaError_t launch_ray_gather(const FrustumArgs &a, const int *ray_pix, int n, float *origins, float *dirs,
+                              cudaStream_t st);
+cudaError_t launch_ray_scatter(const int *ray_pix, int n, const float *t_ray, const int *it_ray, float *t_hit,
+                               int *iters, cudaStream_t st);
+
 // counts: device int64[nseg][SRA_CNT_N]; blk: scratch 2 * nblk
 cudaError_t launch_split_batch(const uint8_t *cls, const sra_node *in, const BatchSplitSeg *segs, int nseg,
                                long long nblk, sra_node *out, sra_node *leaves, unsigned long long *counts,

@@ -100,6 +100,7 @@ struct BatchSegDev {
 // CastRay (Proc. 2) launch parameters and per-slot state.
 struct RayParams {
     const float *origins, *dirs, *f0;
+    const float *t_start, *sigma_start;  // optional per-ray march state to resume from
     float *t_hit;
     int *iters;
     long long n;

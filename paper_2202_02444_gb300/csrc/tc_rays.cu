@@ -239,8 +239,8 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 const unsigned long long q = atomicAdd(p.next, 1ull);
                 if ((long long)q < p.n) {
                     s.idx = (long long)q;
-                    s.t = 0.f;
-                    s.sigma = p.sigma0;
+                    s.t = p.t_start ? p.t_start[q] : 0.f;
+                    s.sigma = p.sigma_start ? p.sigma_start[q] : p.sigma0;
                     s.iters = 0;
                     s.f0pos = p.f0[q] >= 0.f;
                     s.live = 1;

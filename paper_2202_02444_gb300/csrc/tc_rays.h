@@ -28,6 +28,7 @@ struct TcRayParams {
     int *status;
     // CastRay (Proc. 2)
     const float *origins, *dirs, *f0;
+    const float *t_start, *sigma_start;  // optional per-ray march state to resume from
     float *t_hit;
     int *iters;
     long long n;

@@ -98,11 +98,13 @@ _lib.sra_classify_and_split_batch.argtypes = [C.POINTER(_vp), C.POINTER(Opts), C
 _lib.sra_mesh_leaves.argtypes = [_vp, C.POINTER(C.c_float), C.POINTER(C.c_float), _vp, C.c_int64, C.c_int32,
                                  _vp, C.c_int64, C.POINTER(C.c_int64), _vp]
 _lib.sra_empty_spheres.argtypes = [_vp, C.POINTER(Opts), _vp, C.c_int64, C.c_float, C.c_int32, _vp, _vp]
+_lib.sra_cast_frustum.argtypes = [_vp, C.POINTER(Opts), C.POINTER(C.c_float), _vp, C.c_int32, C.c_int32,
+                                  C.c_int32, _vp, _vp, C.POINTER(C.c_int64), _vp]
 _lib.sra_serve.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(Opts), C.c_int32,
                            C.POINTER(ServeCfg), C.POINTER(Request), C.c_int64]
 for _f in ("sra_load_mlp", "sra_free_mlp", "sra_bound_boxes", "sra_classify_and_split",
            "sra_cast_rays", "sra_extract_leaves", "sra_eval", "sra_sync_status", "sra_serve",
-           "sra_classify_and_split_batch", "sra_mesh_leaves", "sra_empty_spheres"):
+           "sra_classify_and_split_batch", "sra_mesh_leaves", "sra_empty_spheres", "sra_cast_frustum"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -298,6 +300,21 @@ def empty_spheres(net, points, r_max=1.0, levels=12, opts=None, radius=None, **k
     _check(_lib.sra_empty_spheres(net.handle, C.byref(opts), _ptr(points), n, float(r_max), int(levels),
                                   _ptr(radius), _stream()))
     return radius
+
+
+def cast_frustum(net, eye, dirs, width, height, grid=16, opts=None, **kw):
+    """Frustum ray casting (Sec. 4.3) of a width x height pinhole image:
+    dirs is a CUDA float32 [height*width, 3] tensor of unit pixel directions
+    from eye. Returns (t_hit [H*W], iters [H*W], stats dict)."""
+    opts = opts or make_opts(**kw)
+    _need(dirs, torch.float32, 3, "dirs")
+    n = width * height
+    t_hit = torch.empty(n, dtype=torch.float32, device=dirs.device)
+    iters = torch.empty(n, dtype=torch.int32, device=dirs.device)
+    st = (C.c_int64 * 4)()
+    _check(_lib.sra_cast_frustum(net.handle, C.byref(opts), (C.c_float * 3)(*[float(v) for v in eye]), _ptr(dirs),
+                                 int(width), int(height), int(grid), _ptr(t_hit), _ptr(iters), st, _stream()))
+    return t_hit, iters, {"rounds": st[0], "frustum_boxes": st[1], "rays": st[2]}
 
 
 def cast_rays(net, origins, dirs, opts=None, t_hit=None, iters=None, **kw):
