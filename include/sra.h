@@ -118,7 +118,11 @@ typedef struct {
                               multiple of 32 in [32, 1024], capped by what the
                               noise-column count allows (the tile shape the
                               autotuner chooses) */
-    int32_t reserved;
+    int32_t converge;    /* sra_classify_and_split / sra_extract_leaves: 1 = also the
+                            convergence test of Proc. 3: an UNKNOWN node narrower than
+                            delta / sqrt(3) whose six face centres take both signs is
+                            returned as a leaf (counts[SRA_CNT_CONVERGED]); 0 = fixed
+                            depth only */
 } sra_opts;
 
 /* Octree / k-d node: integer cell coordinates at `level` inside the root box
@@ -137,6 +141,7 @@ enum {
     SRA_CNT_NEGATIVE = 3, /* nodes classified NEGATIVE */
     SRA_CNT_UNKNOWN = 4,  /* nodes classified UNKNOWN */
     SRA_CNT_RECHECKED = 5,/* nodes re-bounded in FP64 */
+    SRA_CNT_CONVERGED = 6,/* UNKNOWN nodes returned by the convergence test (opts->converge) */
     SRA_CNT_N = 8
 };
 

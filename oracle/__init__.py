@@ -85,6 +85,10 @@ def lib():
         L.orc_build_tree.restype = C.c_int64
         L.orc_build_tree.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
                                      C.c_int, C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]
+        L.orc_build_tree_conv.restype = C.c_int64
+        L.orc_build_tree_conv.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
+                                          C.c_int, C.c_double, C.c_void_p, C.c_int64,
+                                          C.POINTER(C.c_int64)]
         L.orc_classify_nodes.argtypes = [C.POINTER(_Net), C.POINTER(_Opts), dp, dp, C.c_int,
                                          C.c_int64, C.c_void_p, C.POINTER(C.c_int32), dp, dp,
                                          dp, C.c_int]
@@ -178,18 +182,24 @@ def bound_boxes(net, centers, halfw, arith="fixed", K=0, slope="chebyshev", nthr
 
 
 def build_tree(net, xl, xu, max_level, split=OCTREE, arith="fixed", K=0,
-               slope="chebyshev", cap=1 << 22):
-    """Proc. 3 to a fixed depth: (nodes with cls, counts[pos, neg, unk, calls])."""
+               slope="chebyshev", cap=1 << 22, delta=None):
+    """Proc. 3: (nodes with cls, counts[pos, neg, unk, calls(, converged)]).
+    Fixed depth; with delta, also the convergence test for small nodes."""
     n = _net(net)
     o = _opts(arith, K, slope)
     xl = np.ascontiguousarray(np.asarray(xl, np.float64).reshape(3))
     xu = np.ascontiguousarray(np.asarray(xu, np.float64).reshape(3))
     out = np.zeros(cap, NODE_CDT)
-    counts = (C.c_int64 * 4)()
-    m = lib().orc_build_tree(C.byref(n.s), C.byref(o), _dp(xl), _dp(xu), int(max_level),
-                             int(split), out.ctypes.data, cap, counts)
+    if delta is None:
+        counts = (C.c_int64 * 4)()
+        m = lib().orc_build_tree(C.byref(n.s), C.byref(o), _dp(xl), _dp(xu), int(max_level),
+                                 int(split), out.ctypes.data, cap, counts)
+    else:
+        counts = (C.c_int64 * 5)()
+        m = lib().orc_build_tree_conv(C.byref(n.s), C.byref(o), _dp(xl), _dp(xu), int(max_level),
+                                      int(split), float(delta), out.ctypes.data, cap, counts)
     if m > cap:
-        return build_tree(net, xl, xu, max_level, split, arith, K, slope, cap=int(m))
+        return build_tree(net, xl, xu, max_level, split, arith, K, slope, cap=int(m), delta=delta)
     return out[:m].copy(), np.array(list(counts), np.int64)
 
 

@@ -593,7 +593,8 @@ typedef struct {
     int max_level, split;
     orc_node *out;
     int64_t cap, n;
-    int64_t counts[4];
+    int64_t counts[5];
+    double delta;  /* > 0: the convergence test of Proc. 3 for small nodes */
 } tree_ctx;
 
 static void tree_emit(tree_ctx *t, orc_node nd, int cls) {
@@ -616,6 +617,30 @@ static void tree_rec(tree_ctx *t, orc_node nd) {
     int cls = orc_range_bound(t->net, t->o, c, axes, 3, &l, &h, &y0, &r);
     t->counts[3]++;
     if (cls != ORC_UNKNOWN) { tree_emit(t, nd, cls); return; }
+    /* convergence of Proc. 3: a node narrower than delta / sqrt(3) whose
+       sample points, one per face (the face centres), take both signs lies
+       within delta of the level set and is returned as it is */
+    if (t->delta > 0.0) {
+        double wmax = 0.0;
+        for (int d = 0; d < 3; ++d)
+            if (hi[d] - lo[d] > wmax) wmax = hi[d] - lo[d];
+        if (wmax < t->delta / sqrt(3.0)) {
+            int neg = 0, pos = 0;
+            for (int d = 0; d < 3; ++d)
+                for (int side = 0; side < 2; ++side) {
+                    double pf[3] = {c[0], c[1], c[2]};
+                    pf[d] = side ? hi[d] : lo[d];
+                    const double f = orc_eval(t->net, pf);
+                    neg |= f < 0.0;
+                    pos |= f > 0.0;
+                }
+            if (neg && pos) {
+                t->counts[4]++;
+                tree_emit(t, nd, ORC_UNKNOWN);
+                return;
+            }
+        }
+    }
     /* fixed-depth stop (the alternative named in Proc. 3 and used by Sec. 4.7) */
     if (nd.level >= t->max_level) { tree_emit(t, nd, ORC_UNKNOWN); return; }
     if (t->split == ORC_SPLIT_OCTREE) {
@@ -656,6 +681,22 @@ int64_t orc_build_tree(const orc_net *net, const orc_opts *o, const double *xl,
     tree_rec(&t, root);
     if (counts)
         for (int k = 0; k < 4; ++k) counts[k] = t.counts[k];
+    return t.n;
+}
+
+int64_t orc_build_tree_conv(const orc_net *net, const orc_opts *o, const double *xl,
+                            const double *xu, int max_level, int split, double delta,
+                            orc_node *out, int64_t cap, int64_t *counts) {
+    tree_ctx t;
+    memset(&t, 0, sizeof(t));
+    t.net = net; t.o = o; t.xl = xl; t.xu = xu;
+    t.max_level = max_level; t.split = split;
+    t.out = out; t.cap = cap;
+    t.delta = delta;
+    orc_node root = {0, 0, 0, 0, 0};
+    tree_rec(&t, root);
+    if (counts)
+        for (int k = 0; k < 5; ++k) counts[k] = t.counts[k];
     return t.n;
 }
 

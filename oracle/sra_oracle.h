@@ -86,6 +86,15 @@ int64_t orc_build_tree(const orc_net *net, const orc_opts *o, const double *xl,
                        const double *xu, int max_level, int split,
                        orc_node *out, int64_t cap, int64_t *counts);
 
+/* orc_build_tree with the convergence test of Proc. 3 as well: an UNKNOWN
+ * node narrower than delta / sqrt(3) (widest side) whose six face centres
+ * take both signs (some f < 0 and some f > 0) is returned as an UNKNOWN
+ * leaf; other nodes continue to max_level. counts[4] receives the number of
+ * nodes returned by that test. */
+int64_t orc_build_tree_conv(const orc_net *net, const orc_opts *o, const double *xl,
+                            const double *xu, int max_level, int split, double delta,
+                            orc_node *out, int64_t cap, int64_t *counts);
+
 /* RangeBound for a list of tree nodes (the per-node step of Proc. 3). */
 void orc_classify_nodes(const orc_net *net, const orc_opts *o, const double *xl,
                         const double *xu, int split, int64_t n,

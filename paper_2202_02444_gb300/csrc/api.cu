@@ -134,6 +134,8 @@ sra_status check_opts(const sra_opts *o) {
         return fail(SRA_EINVAL, "unknown precision %d", o->precision);
     if (o->split != SRA_SPLIT_OCTREE && o->split != SRA_SPLIT_KD)
         return fail(SRA_EINVAL, "unknown split %d", o->split);
+    if (o->converge != 0 && (o->converge != 1 || !(o->delta > 0.f)))
+        return fail(SRA_EINVAL, "converge must be 0 or 1, and needs delta > 0");
     if (o->block_threads != 0 && (o->block_threads < 32 || o->block_threads > 1024 || o->block_threads % 32))
         return fail(SRA_EINVAL, "block_threads %d: 0 or a multiple of 32 in [32, 1024]", o->block_threads);
     if (!(o->recheck_band >= 0.f)) return fail(SRA_EINVAL, "recheck_band must be >= 0");
@@ -814,6 +816,36 @@ sra_status sra_classify_and_split(const sra_net *n, const sra_opts *o, const flo
     if ((r = bound_with_recheck(n, o, src, bo, n_in,
                                 (unsigned long long *)(counts + SRA_CNT_RECHECKED), st)))
         return r;
+    Scratch scv;
+    if (o->converge) {  // the convergence test of Proc. 3 on the small UNKNOWN nodes
+        const size_t b_l = align16((size_t)n_in * 4), b_i = align16((size_t)n_in * 24),
+                     b_p = align16((size_t)n_in * 72), b_v = align16((size_t)n_in * 24);
+        if ((r = scratch_alloc(scv, b_l + b_i + b_p + b_v + 16, st))) return r;
+        char *q = (char *)scv.p;
+        int *list = (int *)q, *iota = (int *)(q + b_l);
+        float *pts = (float *)(q + b_l + b_i), *vals = (float *)(q + b_l + b_i + b_p);
+        int *cc = (int *)(q + b_l + b_i + b_p + b_v);
+        SRA_CK(cudaMemsetAsync(cc, 0, 16, st));
+        const float wlim = (float)((double)o->delta / std::sqrt(3.0));
+        cudaError_t e = launch_conv_points(src, cls, n_in, wlim, list, &cc[0], &cc[1], pts, st);
+        if (e == cudaSuccess) e = launch_iota(iota, 6 * n_in, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "convergence points: %s", cudaGetErrorString(e));
+        sra_opts eo;
+        sra_default_opts(&eo);
+        eo.arith = SRA_ARITH_INTERVAL;  // zero-width intervals: the plain forward pass
+        BoxSrc ps;
+        memset(&ps, 0, sizeof ps);
+        ps.kind = SRC_POINTS;
+        ps.centers = pts;
+        ps.list = iota;
+        ps.list_count = &cc[1];
+        BoundOut po;
+        memset(&po, 0, sizeof po);
+        po.lo = vals;
+        if ((r = run_bound(n, &eo, false, 1, ps, po, 6 * n_in, st))) return r;
+        if ((e = launch_conv_mark(list, &cc[0], n_in, vals, cls, st)) != cudaSuccess)
+            return fail(SRA_ECUDA, "convergence marks: %s", cudaGetErrorString(e));
+    }
     SplitArgs a;
     memset(&a, 0, sizeof a);
     a.cls = cls;
@@ -846,8 +878,8 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     for (int k = 0; k < n_nets; ++k) {
         if ((r = check_net(nets[k]))) return r;
         if ((r = check_opts(&opts[k]))) return r;
-        if (opts[k].precision != SRA_PREC_FP32 || opts[k].recheck)
-            return fail(SRA_EUNSUPPORTED, "batched rounds run in FP32 without re-check (opts[%d])", k);
+        if (opts[k].precision != SRA_PREC_FP32 || opts[k].recheck || opts[k].converge)
+            return fail(SRA_EUNSUPPORTED, "batched rounds run in FP32 without re-check or convergence test (opts[%d])", k);
     }
     cudaStream_t st = as_stream(stream);
     unsigned char n3[kMaxKdLevels][3], axis[kMaxKdLevels];
@@ -1186,6 +1218,7 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
     size_t capA = 0, capB = 0;
     sra_status status = SRA_OK;
     int64_t hc[SRA_CNT_N] = {0};
+    int64_t leaves_found = 0;
     long long ncur = 1;
     keep_pool_memory();
     auto grow = [&](sra_node **b, size_t *c, size_t need) -> sra_status {
@@ -1217,8 +1250,11 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
         if ((status = grow(&bufB, &capB, next > 0 ? next : 1)) != SRA_OK) break;
         e = cudaMemsetAsync(dcounts, 0, SRA_CNT_N * sizeof(int64_t), st);
         if (e != cudaSuccess) { status = fail(SRA_ECUDA, "memset: %s", cudaGetErrorString(e)); break; }
+        // leaves of every level go after those already found (the convergence
+        // test returns leaves above the last level)
+        const int64_t lcap = cap > leaves_found ? cap - leaves_found : 0;
         status = sra_classify_and_split(n, o, xl, xu, bufA, ncur, depth, bufB, (int64_t)next,
-                                        leaves, cap, dcounts, stream);
+                                        lcap > 0 ? leaves + leaves_found : nullptr, lcap, dcounts, stream);
         if (status) break;
         e = cudaMemcpyAsync(hc, dcounts, sizeof hc, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1229,12 +1265,12 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
             level_counts[level * 3 + 2] = hc[SRA_CNT_UNKNOWN];
         }
         ncur = hc[SRA_CNT_CHILDREN];
+        leaves_found += hc[SRA_CNT_LEAVES];
         std::swap(bufA, bufB);
         std::swap(capA, capB);
         if (ncur == 0 && level < depth) {
             for (int k = level + 1; level_counts && k <= depth; ++k)
                 level_counts[k * 3 + 0] = level_counts[k * 3 + 1] = level_counts[k * 3 + 2] = 0;
-            hc[SRA_CNT_LEAVES] = 0;
             break;
         }
     }
@@ -1242,9 +1278,9 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
     if (bufB) cudaFreeAsync(bufB, st);
     cudaFreeAsync(dcounts, st);
     if (status) return status;
-    *n_leaves = hc[SRA_CNT_LEAVES];
-    if (hc[SRA_CNT_LEAVES] > cap)
-        return fail(SRA_ECAPACITY, "%lld leaves, capacity %lld", (long long)hc[SRA_CNT_LEAVES], (long long)cap);
+    *n_leaves = leaves_found;
+    if (leaves_found > cap)
+        return fail(SRA_ECAPACITY, "%lld leaves, capacity %lld", (long long)leaves_found, (long long)cap);
     return SRA_OK;
 }
 
@@ -1332,6 +1368,7 @@ extern "C" sra_status sra_classify_and_split_noalloc(
     if ((cap_out > 0 && !out) || (cap_leaves > 0 && !leaves)) return fail(SRA_EINVAL, "null output buffer");
     if (o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16)
         return fail(SRA_EUNSUPPORTED, "the allocation-free round runs in FP32 or FP64");
+    if (o->converge) return fail(SRA_EUNSUPPORTED, "the allocation-free round has no convergence test");
     void *scratch = nullptr;
     if ((r = noalloc_scratch(&scratch))) return r;  // before any early return for n_in == 0
     if (n_in == 0) return SRA_OK;

@@ -24,7 +24,8 @@ __device__ __forceinline__ void emit_counts(const SplitArgs &a, long long i, int
     else if (k == SRA_NEGATIVE) neg = 1;
     else {
         unk = 1;
-        if ((int)a.in[i].level < a.max_level) ch = (a.split == SRA_SPLIT_OCTREE) ? 8 : 2;
+        // a node of the convergence test is a leaf at any level
+        if (k != kClsConverged && (int)a.in[i].level < a.max_level) ch = (a.split == SRA_SPLIT_OCTREE) ? 8 : 2;
         else lf = 1;
     }
 }
@@ -71,17 +72,19 @@ __global__ void __launch_bounds__(kSplitBlock) split_count_kernel(SplitArgs a) {
     block_scan2(ch, lf, ea, eb, ta, tb);
     // per-class tallies (sums; order does not matter)
     const int lane = threadIdx.x & 31;
-    int p = pos, q = neg, u = unk;
+    int p = pos, q = neg, u = unk, cv = (i < a.n && a.cls[i] == kClsConverged) ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         p += __shfl_xor_sync(0xffffffffu, p, o);
         q += __shfl_xor_sync(0xffffffffu, q, o);
         u += __shfl_xor_sync(0xffffffffu, u, o);
+        cv += __shfl_xor_sync(0xffffffffu, cv, o);
     }
     if (lane == 0) {
         if (p) atomicAdd(&a.counts[SRA_CNT_POSITIVE], (unsigned long long)p);
         if (q) atomicAdd(&a.counts[SRA_CNT_NEGATIVE], (unsigned long long)q);
         if (u) atomicAdd(&a.counts[SRA_CNT_UNKNOWN], (unsigned long long)u);
+        if (cv) atomicAdd(&a.counts[SRA_CNT_CONVERGED], (unsigned long long)cv);
     }
     if (threadIdx.x == 0) {
         a.blk[2 * blockIdx.x] = ta;

@@ -98,6 +98,15 @@ cudaError_t launch_ray_gather(const FrustumArgs &a, const int *ray_pix, int n, f
 cudaError_t launch_ray_scatter(const int *ray_pix, int n, const float *t_ray, const int *it_ray, float *t_hit,
                                int *iters, cudaStream_t st);
 
+// Convergence test of Proc. 3 (opts->converge): class code of the nodes it
+// returns as leaves, and the launches that find them.
+constexpr uint8_t kClsConverged = 3;
+cudaError_t launch_conv_points(const BoxSrc &geo, const uint8_t *cls, long long n, float wlim, int *list,
+                               int *count, int *count6, float *pts, cudaStream_t st);
+cudaError_t launch_iota(int *a, long long n, cudaStream_t st);
+cudaError_t launch_conv_mark(const int *list, const int *count, long long n_hint, const float *vals, uint8_t *cls,
+                             cudaStream_t st);
+
 // counts: device int64[nseg][SRA_CNT_N]; blk: scratch 2 * nblk
 cudaError_t launch_split_batch(const uint8_t *cls, const sra_node *in, const BatchSplitSeg *segs, int nseg,
                                long long nblk, sra_node *out, sra_node *leaves, unsigned long long *counts,

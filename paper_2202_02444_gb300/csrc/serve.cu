@@ -80,6 +80,7 @@ struct Slot {
     // leaf job state
     int level = 0;
     long long ncur = 0;
+    int64_t leaves_found = 0;  // leaves of earlier levels (convergence test)
     sra_node *bufA = nullptr, *bufB = nullptr;
     int64_t *dcounts = nullptr;
 };
@@ -179,8 +180,10 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
         const sra_request &q = reqs[s.req];
         if (cudaMemsetAsync(s.dcounts, 0, SRA_CNT_N * sizeof(int64_t), s.st) != cudaSuccess)
             return SRA_ECUDA;
+        const int64_t lcap = q.cap > s.leaves_found ? q.cap - s.leaves_found : 0;
         sra_status r = sra_classify_and_split(nets[q.net], &forms[q.form], kRootLo, kRootHi, s.bufA, s.ncur,
-                                              q.depth, s.bufB, q.cap, q.leaves, q.cap, s.dcounts, s.st);
+                                              q.depth, s.bufB, q.cap, lcap > 0 ? q.leaves + s.leaves_found : nullptr,
+                                              lcap, s.dcounts, s.st);
         if (r) return r;
         if (cudaMemcpyAsync(s.hcounts, s.dcounts, SRA_CNT_N * sizeof(int64_t), cudaMemcpyDeviceToHost, s.st) !=
                 cudaSuccess ||
@@ -210,6 +213,7 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
             s.dcounts = (int64_t *)(base + 2 * buf);
             s.level = 0;
             s.ncur = 1;
+            s.leaves_found = 0;
             // the root node (level 0, index 0) is all zero bytes
             r = cudaMemsetAsync(s.bufA, 0, sizeof(sra_node), s.st) == cudaSuccess ? SRA_OK : SRA_ECUDA;
             if (!r) r = launch_level(s);
@@ -226,8 +230,9 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
         }
         const int64_t *hc = s.hcounts;
         q.levels = s.level + 1;
+        s.leaves_found += hc[SRA_CNT_LEAVES];
         if (s.level == q.depth) {
-            q.n_out = hc[SRA_CNT_LEAVES];
+            q.n_out = s.leaves_found;
             finish(s, q.n_out > q.cap ? SRA_ECAPACITY : SRA_OK);
             return;
         }
@@ -238,8 +243,8 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
             return;
         }
         if (children == 0) {
-            q.n_out = 0;
-            finish(s, SRA_OK);
+            q.n_out = s.leaves_found;
+            finish(s, q.n_out > q.cap ? SRA_ECAPACITY : SRA_OK);
             return;
         }
         std::swap(s.bufA, s.bufB);

@@ -26,7 +26,7 @@ ARITH = {"interval": 0, "fixed": 1, "truncate": 2, "full": 3}
 SLOPE = {"chebyshev": 0, "minrange": 1}
 PRECISION = {"fp32": 0, "fp64": 1, "bf16_sound": 2, "bf16": 3}
 SPLIT = {"octree": 0, "kd": 1}
-CNT_CHILDREN, CNT_LEAVES, CNT_POSITIVE, CNT_NEGATIVE, CNT_UNKNOWN, CNT_RECHECKED = range(6)
+CNT_CHILDREN, CNT_LEAVES, CNT_POSITIVE, CNT_NEGATIVE, CNT_UNKNOWN, CNT_RECHECKED, CNT_CONVERGED = range(7)
 CNT_N = 8
 
 NODE_DTYPE = np.dtype([("ix", "<u2"), ("iy", "<u2"), ("iz", "<u2"), ("level", "<u2")])
@@ -50,7 +50,7 @@ class Opts(C.Structure):
                 ("split", C.c_int32), ("delta", C.c_float), ("t_max", C.c_float),
                 ("sigma0", C.c_float), ("eta_plus", C.c_float), ("eta_minus", C.c_float),
                 ("safety", C.c_float), ("max_iters", C.c_int64),
-                ("block_threads", C.c_int32), ("reserved", C.c_int32)]
+                ("block_threads", C.c_int32), ("converge", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -120,7 +120,8 @@ def _check(code):
 
 def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=False,
               recheck_band=1e-5, split="octree", delta=None, t_max=None, sigma0=None,
-              eta_plus=None, eta_minus=None, safety=None, max_iters=None, block_threads=0):
+              eta_plus=None, eta_minus=None, safety=None, max_iters=None, block_threads=0,
+              converge=False):
     o = Opts()
     _lib.sra_default_opts(C.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -139,6 +140,7 @@ def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=F
     if max_iters is not None:
         o.max_iters = int(max_iters)
     o.block_threads = int(block_threads)
+    o.converge = int(bool(converge))
     return o
 
 

@@ -170,3 +170,45 @@ def test_plane_net_exact_leaves(sra):
     allow = {(int(a), int(b), int(c), 5) for a, b, c in I[may]}
     assert need <= got and got <= allow
     net.close()
+
+
+@pytest.mark.parametrize("delta,depth", [(0.1, 7), (0.03, 8)])
+def test_convergence_test_matches_oracle(sra, delta, depth):
+    """Proc. 3 with its convergence test (opts.converge): the UNKNOWN leaves,
+    at every level, equal the oracle's except where an ancestor's bound or a
+    face sample lies within FP32 rounding of zero."""
+    mlp = wl.make_mlp([32, 32], "elu", seed=3)
+    net = sra.Net(mlp)
+    try:
+        leaves, counts = sra.extract_leaves(net, depth, XL, XU, arith="fixed", delta=delta, converge=True)
+        torch.cuda.synchronize()
+        got_nodes = sra.tensor_to_nodes(leaves)
+    finally:
+        net.close()
+    got = keyset(got_nodes)
+    nodes, ocnt = oracle.build_tree(mlp, XL, XU, depth, arith="fixed", delta=delta)
+    unk = nodes[nodes["cls"] == oracle.UNKNOWN]
+    want = keyset(unk)
+    assert ocnt[4] > 0 and len(want) > 100
+    assert (got_nodes["level"] < depth).any()  # leaves above the depth cap were returned
+    diff = got ^ want
+
+    def face_near_zero(k):
+        ix, iy, iz, lv = k
+        w = 2.0 / (1 << lv)
+        lo = -1.0 + np.array([ix, iy, iz]) * w
+        c = lo + 0.5 * w
+        pts = np.repeat(c[None], 6, 0)
+        for f in range(6):
+            pts[f, f >> 1] = lo[f >> 1] + (w if f & 1 else 0.0)
+        return np.abs(oracle.evaluate(mlp, pts)).min() < 1e-5
+
+    def explained(k):
+        # the node, an ancestor, or the ancestor's face test sits within rounding of zero
+        ix, iy, iz, lv = k
+        chain = [(ix >> s, iy >> s, iz >> s, lv - s) for s in range(lv + 1)]
+        return ancestors_near_zero(mlp, k, oracle.OCTREE, "fixed", 0) or any(face_near_zero(a) for a in chain)
+
+    unexplained = [k for k in diff if not explained(k)]
+    assert not unexplained, unexplained[:5]
+    assert len(diff) <= 0.01 * len(want)
