@@ -568,10 +568,11 @@ def main():
         net_small.close()
 
     # frustum ray casting (Sec. 4.3) against per-pixel CastRay, 512x512 image of
-    # the ReLU 3-32-32-1 network (the networks with surfaces in view)
+    # an ELU 3-[128]x4-1 network with a surface in view (seed 23: half of the
+    # root box negative)
     frustum = None
     if rank == 0:
-        net_small = sra.Net(wl.net_small_relu())
+        net_small = sra.Net(wl.make_mlp([128] * 4, "elu", seed=23))
         Wf = Hf = 512
         of, df = wl.camera_rays(Wf, Hf)
         dft, oft = torch.from_numpy(df).to(dev), torch.from_numpy(of).to(dev)
@@ -590,8 +591,8 @@ def main():
         agree = (fa == fb)
         agree[fa & fb] &= np.abs(a_[fa & fb] - b_[fa & fb]) <= 1e-3 * 1.0001 + 1e-6
         npx = Wf * Hf
-        frustum = {"workload": "512x512 camera at (0,0,3) vs ReLU 3-32-32-1, affine-fixed FP32, delta 1e-3, "
-                               "16x16 coarse frusta",
+        frustum = {"workload": "512x512 camera at (0,0,3) vs ELU 3-[128]x4-1 (He init, seed 23), affine-fixed "
+                               "FP32, delta 1e-3, 16x16 coarse frusta",
                    "frustum_s": t1 - t0, "per_ray_s": t2 - t1,
                    "frustum_steps_per_pixel": (fst["frustum_boxes"] + int(itf.sum())) / npx,
                    "per_ray_steps_per_pixel": int(itr.sum()) / npx,

@@ -1128,7 +1128,7 @@ sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *ey
     const size_t b_fr = align16((size_t)npix * sizeof(Frustum)), b_v3 = align16((size_t)npix * 12),
                  b_1 = align16((size_t)npix), b_4 = align16((size_t)npix * 4);
     Scratch sc;
-    if ((r = scratch_alloc(sc, 2 * b_fr + 2 * b_v3 + b_1 + 3 * b_4 + 64, st))) return r;
+    if ((r = scratch_alloc(sc, 2 * b_fr + 2 * b_v3 + b_1 + 4 * b_4 + 64, st))) return r;
     char *p = (char *)sc.p;
     Frustum *fr[2] = {(Frustum *)p, (Frustum *)(p + b_fr)};
     p += 2 * b_fr;
@@ -1138,41 +1138,47 @@ sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *ey
     p += b_1;
     int *ray_pix = (int *)p;
     float *ray_t = (float *)(p + b_4), *ray_sigma = (float *)(p + 2 * b_4);
-    p += 3 * b_4;
-    int *cnt = (int *)p;  // [0] current frusta, [1] next frusta, [2] rays, [4..5] recheck tally
+    int *iota = (int *)(p + 3 * b_4);
+    p += 4 * b_4;
+    // [0] current frusta, [1] next frusta, [2] rays, [3] boxes bounded, [4..5] recheck tally
+    int *cnt = (int *)p;
     SRA_CK(cudaMemsetAsync(cnt, 0, 64, st));
     cudaError_t e = launch_frustum_init(a, grid, fr[0], &cnt[0], st);
+    if (e == cudaSuccess) e = launch_iota(iota, npix, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "frustum init: %s", cudaGetErrorString(e));
-    const int tw = (W + grid - 1) / grid, th = (Hh + grid - 1) / grid;
-    long long nf = (long long)((W + tw - 1) / tw) * ((Hh + th - 1) / th);
+    // Rounds run from device-side counts; the host reads them every kBatch
+    // rounds (a round with no frusta left launches kernels that do nothing).
+    constexpr int kBatch = 8;
     long long rounds = 0, boxes = 0;
-    int host_cnt[3] = {0, 0, 0};
+    int host_cnt[4] = {1, 0, 0, 0};
     int cur = 0;
-    while (nf > 0) {
-        if (++rounds > 1000000) return fail(SRA_ETIMEOUT, "frustum march did not finish");
-        SRA_CK(cudaMemsetAsync(&cnt[1], 0, sizeof(int), st));
-        if ((e = launch_frustum_boxes(a, fr[cur], &cnt[0], nf, centers, halfw, st)) != cudaSuccess)
-            return fail(SRA_ECUDA, "frustum boxes: %s", cudaGetErrorString(e));
-        BoxSrc src;
-        memset(&src, 0, sizeof src);
-        src.kind = SRC_BOXES;
-        src.centers = centers;
-        src.halfw = halfw;
-        src.n = nf;
-        BoundOut out;
-        memset(&out, 0, sizeof out);
-        out.cls = cls;
-        if ((r = bound_with_recheck(n, &bo, src, out, nf, (unsigned long long *)&cnt[4], st))) return r;
-        if ((e = launch_frustum_update(a, fr[cur], &cnt[0], nf, cls, fr[cur ^ 1], &cnt[1], ray_pix, ray_t, ray_sigma,
-                                       &cnt[2], t_hit, iters, st)) != cudaSuccess)
-            return fail(SRA_ECUDA, "frustum update: %s", cudaGetErrorString(e));
-        SRA_CK(cudaMemcpyAsync(&cnt[0], &cnt[1], sizeof(int), cudaMemcpyDeviceToDevice, st));
-        SRA_CK(cudaMemcpyAsync(host_cnt, cnt, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    while (host_cnt[0] > 0) {
+        for (int k = 0; k < kBatch; ++k) {
+            if (++rounds > 1000000) return fail(SRA_ETIMEOUT, "frustum march did not finish");
+            SRA_CK(cudaMemsetAsync(&cnt[1], 0, sizeof(int), st));
+            if ((e = launch_frustum_boxes(a, fr[cur], &cnt[0], npix, centers, halfw, st)) != cudaSuccess)
+                return fail(SRA_ECUDA, "frustum boxes: %s", cudaGetErrorString(e));
+            BoxSrc src;
+            memset(&src, 0, sizeof src);
+            src.kind = SRC_BOXES;
+            src.centers = centers;
+            src.halfw = halfw;
+            src.list = iota;  // box b is frustum b, count on the device
+            src.list_count = &cnt[0];
+            BoundOut out;
+            memset(&out, 0, sizeof out);
+            out.cls = cls;
+            if ((r = bound_with_recheck(n, &bo, src, out, npix, (unsigned long long *)&cnt[4], st))) return r;
+            if ((e = launch_frustum_update(a, fr[cur], &cnt[0], npix, cls, fr[cur ^ 1], &cnt[1], ray_pix, ray_t,
+                                           ray_sigma, &cnt[2], &cnt[3], t_hit, iters, st)) != cudaSuccess)
+                return fail(SRA_ECUDA, "frustum update: %s", cudaGetErrorString(e));
+            SRA_CK(cudaMemcpyAsync(&cnt[0], &cnt[1], sizeof(int), cudaMemcpyDeviceToDevice, st));
+            cur ^= 1;
+        }
+        SRA_CK(cudaMemcpyAsync(host_cnt, cnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
         SRA_CK(cudaStreamSynchronize(st));
-        boxes += nf;
-        nf = host_cnt[0];
-        cur ^= 1;
     }
+    boxes = host_cnt[3];
     const int nr = host_cnt[2];
     if (stats) {
         stats[0] = rounds;

@@ -87,8 +87,9 @@ __global__ void frustum_box_kernel(FrustumArgs a, const Frustum *fr, const int *
 
 __global__ void frustum_update_kernel(FrustumArgs a, const Frustum *fr, const int *count, const uint8_t *cls,
                                       Frustum *out, int *out_count, int *ray_pix, float *ray_t, float *ray_sigma,
-                                      int *ray_count, float *t_hit, int *iters) {
+                                      int *ray_count, int *boxes, float *t_hit, int *iters) {
     const int n = *count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(boxes, n);  // frustum boxes bounded this round
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Frustum f = fr[i];
         if (cls[i] != SRA_UNKNOWN) {
@@ -172,9 +173,10 @@ cudaError_t launch_frustum_boxes(const FrustumArgs &a, const Frustum *fr, const 
 
 cudaError_t launch_frustum_update(const FrustumArgs &a, const Frustum *fr, const int *count, long long n_hint,
                                   const uint8_t *cls, Frustum *out, int *out_count, int *ray_pix, float *ray_t,
-                                  float *ray_sigma, int *ray_count, float *t_hit, int *iters, cudaStream_t st) {
+                                  float *ray_sigma, int *ray_count, int *boxes, float *t_hit, int *iters,
+                                  cudaStream_t st) {
     frustum_update_kernel<<<blocks_for(n_hint), 256, 0, st>>>(a, fr, count, cls, out, out_count, ray_pix, ray_t,
-                                                                ray_sigma, ray_count, t_hit, iters);
+                                                                ray_sigma, ray_count, boxes, t_hit, iters);
     return cudaGetLastError();
 }
 

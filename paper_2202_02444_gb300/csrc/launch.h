@@ -92,7 +92,8 @@ cudaError_t launch_frustum_boxes(const FrustumArgs &a, const Frustum *fr, const 
                                  float *centers, float *halfw, cudaStream_t st);
 cudaError_t launch_frustum_update(const FrustumArgs &a, const Frustum *fr, const int *count, long long n_hint,
                                   const uint8_t *cls, Frustum *out, int *out_count, int *ray_pix, float *ray_t,
-                                  float *ray_sigma, int *ray_count, float *t_hit, int *iters, cudaStream_t st);
+                                  float *ray_sigma, int *ray_count, int *boxes, float *t_hit, int *iters,
+                                  cudaStream_t st);
 cudaError_t launch_ray_gather(const FrustumArgs &a, const int *ray_pix, int n, float *origins, float *dirs,
                               cudaStream_t st);
 cudaError_t launch_ray_scatter(const int *ray_pix, int n, const float *t_ray, const int *it_ray, float *t_hit,
