@@ -174,6 +174,22 @@ struct Scratch {
     }
 };
 
+// Regions of one scratch allocation, taken in order. A sizing pass (base
+// null) adds up the bytes; the carving pass over the allocation hands out
+// 16-byte-aligned regions and reports a region that would pass its end.
+struct Carve {
+    char *base = nullptr;
+    size_t off = 0, cap = 0;
+    bool overflow = false;
+    template <typename T> T *take(size_t count) {
+        const size_t b = align16(count * sizeof(T));
+        T *q = base ? (T *)(base + off) : nullptr;
+        off += b;
+        if (base && off > cap) overflow = true;
+        return q;
+    }
+};
+
 sra_status scratch_alloc(Scratch &s, size_t bytes, cudaStream_t st) {
     keep_pool_memory();
     s.st = st;
@@ -673,14 +689,25 @@ sra_status sra_empty_spheres(const sra_net *n, const sra_opts *o, const float *p
     if (count == 0) return SRA_OK;
     if (!points || !radius) return fail(SRA_EINVAL, "null points / radius_out");
     cudaStream_t st = as_stream(stream);
-    const size_t b_list = align16((size_t)count * 4), b_hw = align16((size_t)count * 12), b_cls = align16((size_t)count);
+    int *list[2], *cnt;
+    float *halfw;
+    uint8_t *cls;
+    auto carve = [&](Carve &c) {
+        list[0] = c.take<int>(count);
+        list[1] = c.take<int>(count);
+        halfw = c.take<float>(3 * count);
+        cls = c.take<uint8_t>(count);
+        cnt = c.take<int>(16);  // [0], [1]: list counts; [4..5]: recheck tally
+    };
+    Carve sizing;
+    carve(sizing);
     Scratch sc;
-    if ((r = scratch_alloc(sc, 2 * b_list + b_hw + b_cls + 64, st))) return r;
-    char *base = (char *)sc.p;
-    int *list[2] = {(int *)base, (int *)(base + b_list)};
-    float *halfw = (float *)(base + 2 * b_list);
-    uint8_t *cls = (uint8_t *)(base + 2 * b_list + b_hw);
-    int *cnt = (int *)(base + 2 * b_list + b_hw + b_cls);  // [0], [1]: list counts; [4..5]: recheck tally
+    if ((r = scratch_alloc(sc, sizing.off, st))) return r;
+    Carve cv;
+    cv.base = (char *)sc.p;
+    cv.cap = sizing.off;
+    carve(cv);
+    if (cv.overflow) return fail(SRA_ECUDA, "sphere scratch layout exceeds its allocation");
     cudaError_t e = launch_sphere_init(count, list[0], &cnt[0], radius, st);
     if (e != cudaSuccess) return fail(SRA_ECUDA, "sphere init: %s", cudaGetErrorString(e));
     float rk = r_max;
@@ -818,13 +845,23 @@ sra_status sra_classify_and_split(const sra_net *n, const sra_opts *o, const flo
         return r;
     Scratch scv;
     if (o->converge) {  // the convergence test of Proc. 3 on the small UNKNOWN nodes
-        const size_t b_l = align16((size_t)n_in * 4), b_i = align16((size_t)n_in * 24),
-                     b_p = align16((size_t)n_in * 72), b_v = align16((size_t)n_in * 24);
-        if ((r = scratch_alloc(scv, b_l + b_i + b_p + b_v + 16, st))) return r;
-        char *q = (char *)scv.p;
-        int *list = (int *)q, *iota = (int *)(q + b_l);
-        float *pts = (float *)(q + b_l + b_i), *vals = (float *)(q + b_l + b_i + b_p);
-        int *cc = (int *)(q + b_l + b_i + b_p + b_v);
+        int *list, *iota, *cc;
+        float *pts, *vals;
+        auto carve = [&](Carve &c) {
+            list = c.take<int>(n_in);
+            iota = c.take<int>(6 * n_in);
+            pts = c.take<float>(18 * n_in);
+            vals = c.take<float>(6 * n_in);
+            cc = c.take<int>(4);
+        };
+        Carve sizing;
+        carve(sizing);
+        if ((r = scratch_alloc(scv, sizing.off, st))) return r;
+        Carve cv;
+        cv.base = (char *)scv.p;
+        cv.cap = sizing.off;
+        carve(cv);
+        if (cv.overflow) return fail(SRA_ECUDA, "convergence scratch layout exceeds its allocation");
         SRA_CK(cudaMemsetAsync(cc, 0, 16, st));
         const float wlim = (float)((double)o->delta / std::sqrt(3.0));
         cudaError_t e = launch_conv_points(src, cls, n_in, wlim, list, &cc[0], &cc[1], pts, st);
@@ -1125,23 +1162,32 @@ sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *ey
     a.delta = o->delta;
     sra_opts bo = *o;  // frustum boxes: FP32 bounds of the same arithmetic
     bo.precision = SRA_PREC_FP32;
-    const size_t b_fr = align16((size_t)npix * sizeof(Frustum)), b_v3 = align16((size_t)npix * 12),
-                 b_1 = align16((size_t)npix), b_4 = align16((size_t)npix * 4);
+    Frustum *fr[2];
+    float *centers, *halfw, *ray_t, *ray_sigma;
+    uint8_t *cls;
+    int *ray_pix, *iota, *cnt;
+    auto carve = [&](Carve &c) {
+        fr[0] = c.take<Frustum>(npix);
+        fr[1] = c.take<Frustum>(npix);
+        centers = c.take<float>(3 * npix);
+        halfw = c.take<float>(3 * npix);
+        cls = c.take<uint8_t>(npix);
+        ray_pix = c.take<int>(npix);
+        ray_t = c.take<float>(npix);
+        ray_sigma = c.take<float>(npix);
+        iota = c.take<int>(npix);
+        // [0] current frusta, [1] next frusta, [2] rays, [3] boxes bounded, [4..5] recheck tally
+        cnt = c.take<int>(16);
+    };
+    Carve sizing;
+    carve(sizing);
     Scratch sc;
-    if ((r = scratch_alloc(sc, 2 * b_fr + 2 * b_v3 + b_1 + 4 * b_4 + 64, st))) return r;
-    char *p = (char *)sc.p;
-    Frustum *fr[2] = {(Frustum *)p, (Frustum *)(p + b_fr)};
-    p += 2 * b_fr;
-    float *centers = (float *)p, *halfw = (float *)(p + b_v3);
-    p += 2 * b_v3;
-    uint8_t *cls = (uint8_t *)p;
-    p += b_1;
-    int *ray_pix = (int *)p;
-    float *ray_t = (float *)(p + b_4), *ray_sigma = (float *)(p + 2 * b_4);
-    int *iota = (int *)(p + 3 * b_4);
-    p += 4 * b_4;
-    // [0] current frusta, [1] next frusta, [2] rays, [3] boxes bounded, [4..5] recheck tally
-    int *cnt = (int *)p;
+    if ((r = scratch_alloc(sc, sizing.off, st))) return r;
+    Carve cv;
+    cv.base = (char *)sc.p;
+    cv.cap = sizing.off;
+    carve(cv);
+    if (cv.overflow) return fail(SRA_ECUDA, "frustum scratch layout exceeds its allocation");
     SRA_CK(cudaMemsetAsync(cnt, 0, 64, st));
     cudaError_t e = launch_frustum_init(a, grid, fr[0], &cnt[0], st);
     if (e == cudaSuccess) e = launch_iota(iota, npix, st);
