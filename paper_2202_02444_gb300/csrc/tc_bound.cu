@@ -8,7 +8,9 @@
 // runs concurrently. The per-box affine state never leaves the SM:
 //   * operand B of every hidden layer: the 2 x 64 noise columns (BF16) and a
 //     16-column chunk holding each box's center as a BF16 hi/lo pair, written
-//     by the epilogue threads in the K-major 128-byte-swizzled layout;
+//     by the epilogue threads in the K-major 128-byte-swizzled layout; the
+//     chunk follows the noise rows of each K slice, so one MMA of N = 144
+//     covers both;
 //   * operand A: W as BF16 hi + lo (W = W_b + W_r + rho, |rho| <= u_b^2 |W|),
 //     streamed per 64-wide K slice by TMA into a two-stage ring;
 //   * D = (W_b + W_r) [X | c_hi c_lo] accumulates in TMEM (FP32);
@@ -33,6 +35,7 @@ constexpr int NB = 2;        // boxes per tile (one thread group each)
 constexpr int KT = 64;       // kept noise symbols per box
 constexpr int NA = NB * KT;  // noise columns per tile (MMA N)
 constexpr int NCC = 16;      // center-chunk columns (MMA N)
+constexpr int TM_STRIDE = 256;  // TMEM columns per M tile: NA noise then NCC center accumulators
 constexpr int NPART = 4;     // partial sums per output-layer dot product
 constexpr uint32_t kSpin = 1u << 22;
 
@@ -43,10 +46,12 @@ template <int H> struct Layout {
     static constexpr int STAGE = 2 * MT * TILE;             // W_b and W_r tiles of one K slice
     static constexpr int W_OFF = 0;
     static constexpr int XA_OFF = 2 * STAGE;
-    static constexpr int XA_SLICE = NA * 128;
-    static constexpr int XC_OFF = XA_OFF + S * XA_SLICE;
-    static constexpr int XC_SLICE = NCC * 128;
-    static constexpr int F_OFF = XC_OFF + S * XC_SLICE;
+    // operand B, per 64-wide K slice: NA noise rows then NCC center rows,
+    // so one MMA of N = NA + NCC covers both (slice stride 18 KB)
+    static constexpr int XA_SLICE = (NA + NCC) * 128;
+    static constexpr int XC_OFF = XA_OFF + NA * 128;
+    static constexpr int XC_SLICE = XA_SLICE;
+    static constexpr int F_OFF = XA_OFF + S * XA_SLICE;
     static constexpr int NCAND = KT + H;
     static constexpr int V_OFF = F_OFF;                              // v[NB][H]
     static constexpr int XR_OFF = V_OFF + NB * H * 4;                // xr[NB][H]
@@ -55,13 +60,14 @@ template <int H> struct Layout {
     static constexpr int OUT_OFF = PART_OFF + NB * (H / 32) * KT * 4;  // Y,E [NB][NPART][KT+2]
     static constexpr int WOUT_OFF = OUT_OFF + 2 * NB * NPART * (KT + 2) * 4;  // wout[H]
     static constexpr int BOX_OFF = WOUT_OFF + H * 4;                 // box c/h [NB][8]
-    static constexpr int HIST_OFF = BOX_OFF + NB * 8 * 4;            // hist[NB][256]
-    static constexpr int KEEP_OFF = HIST_OFF + NB * 256 * 4;         // keep[NB][NCAND]
-    static constexpr int POS_OFF = ((KEEP_OFF + NB * NCAND) + 15) & ~15;  // pos[NB][NCAND]
-    static constexpr int NEW_OFF = ((POS_OFF + NB * NCAND * 2) + 15) & ~15; // newlist[NB][KT]
+    static constexpr int XP_OFF = BOX_OFF + NB * 8 * 4;              // |W_b| v partials [NB][H]
+    static constexpr int NCH = (KT + H + 31) / 32;                    // candidate chunks of 32
+    static constexpr int KM_OFF = XP_OFF + NB * H * 4;               // kept masks [NB][16]
+    static constexpr int NEW_OFF = KM_OFF + NB * 16 * 4;             // newlist[NB][KT]
     static constexpr int BAR_OFF = ((NEW_OFF + NB * KT * 4) + 15) & ~15;   // 5 mbarriers
     static constexpr int MISC_OFF = BAR_OFF + 64;  // tmem slot, abort, nnew[NB], sel[NB][2]
-    static constexpr int BYTES = MISC_OFF + 64;
+    static constexpr int DUMMY_OFF = MISC_OFF + 64;  // 32 x 16 B sink for dropped columns' stores
+    static constexpr int BYTES = DUMMY_OFF + 512;
     static constexpr int ALLOC = BYTES + 1024;     // + alignment slack
 };
 
@@ -80,6 +86,22 @@ __device__ __forceinline__ void group_sync(int g, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthreads) : "memory");
 }
 
+// (d0, d1) += (a0 * b0, a1 * b1), each rounded up (one paired FMA).
+__device__ __forceinline__ void fma2_ru(float &d0, float &d1, float a0, float a1, float b0, float b1) {
+    unsigned long long A, B, D;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(D) : "f"(d0), "f"(d1));
+    asm("fma.rp.f32x2 %0, %1, %2, %0;" : "+l"(D) : "l"(A), "l"(B));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(D));
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 struct Ctx {
     unsigned char *smem;
     int tid, g, i, wg, lane;  // thread, group (= box), neuron, warp in group, lane
@@ -93,15 +115,14 @@ __device__ __forceinline__ void fail(const Ctx &x, const TcParams &p, int code) 
     atomicExch(p.status, code);
 }
 
-// Outward-rounded range of one row, the ReLU rule and its application.
-// Scales a in place and returns alpha (the caller may rescale a reloaded row
-// bit-identically), gamma, the new center c2 and x_inf.
+// The ReLU rule of App. A Table "affine_nonlinearities" for one neuron whose
+// noise magnitudes sum to sa (rounded up), center c and independent part
+// xinf: outward-rounded range, slope al, new-symbol magnitude ga, new center
+// c2 and the new independent part xi. The sound form adds the rounding of c2
+// and of every al * a entry (and its later BF16 rounding) to xi.
 template <bool SOUND>
-__device__ __forceinline__ void relu_apply(float (&a)[KT], float c, float &xinf, float &c2, float &al,
-                                           float &ga, float u_b2u) {
-    float sa = 0.f;
-#pragma unroll
-    for (int k = 0; k < KT; ++k) sa = ru_add(sa, fabsf(a[k]));
+__device__ __forceinline__ void relu_rule(float sa, float c, float xinf, float u_b2u, float &al, float &ga, float &c2,
+                                          float &xi) {
     const float rad = ru_add(sa, xinf);
     const float lo = rd_add(c, -rad), hi = ru_add(c, rad);
     float be;
@@ -117,185 +138,348 @@ __device__ __forceinline__ void relu_apply(float (&a)[KT], float c, float &xinf,
         be = 0.5f * M;  // exact halving
         ga = be;
     }
-#pragma unroll
-    for (int k = 0; k < KT; ++k) a[k] = al * a[k];
     c2 = fmaf(al, c, be);
-    // |al| x_inf, the rounding of c2, and of every al * a (and its later bf16
-    // rounding) as u_b + 2u relative of sum |a|
-    float xi = __fmul_ru(al, xinf);
+    xi = __fmul_ru(al, xinf);
     if (SOUND) {
         xi = ru_fma(fabsf(c2), 1.1920929e-07f, xi);  // one rounding: <= 2^-23 |c2|
         xi = ru_fma(__fmul_ru(al, sa), u_b2u, xi);
     }
-    xinf = xi;
 }
 
-// Truncate (Sec. 3.3) the group's box after the activation and write its
-// operand rows. Thread i of group g holds the scaled old columns a[0..Ncur)
-// of neuron i, its new symbol gamma and x_inf. The column norms consume a;
-// `reload` rebuilds it bit-identically for the write-back.
-template <int H, bool SOUND, typename Reload>
-__device__ void truncate_and_store(const Ctx &x, const TcParams &p, float (&a)[KT], int Ncur, float gamma,
-                                   float xinf, float c2, Reload reload) {
+// Upper bound of the summed magnitudes of a neuron's BF16 operand entries
+// after truncation: every kept entry is bf16(al * a) (at most (1 + 2^-8)
+// al |a| each, kept or not) and the neuron's own new symbol (at most
+// (1 + 2^-7) ga).
+__device__ __forceinline__ float operand_mag_bound(float al, float sa, float ga) {
+    return ru_mul(ru_add(ru_mul(al, sa), ga), 1.0078125f);
+}
+
+// Top-KT of the group's Ncur + H candidates (Sec. 3.3 truncate), by warp 0
+// of the group alone. The old columns' scores (L1 norms) are summed from the
+// per-warp partials, the new symbols' magnitudes score[Ncur..) were written
+// by their neurons; the caller has synchronised the group after both. The
+// selection key is the score's top 16 bits (the BF16 truncation of a
+// non-negative float: the scores come from BF16 operands and carry their
+// 2^-8 relative error, so lower bits are not significant); non-negative
+// floats order like their bit patterns. The KT-th largest key T is found by
+// bisection, two bits per step (three warp-wide counts), after a check
+// whether at most KT keys are non-zero (then T = 0). Ties at T go to the
+// lower candidate index, and kept columns stay in candidate order. Writes the kept mask of every chunk of 32 candidates,
+// the kept new symbols newlist[q] = position | neuron << 16 and nnew to
+// shared memory, valid after the caller's next group_sync.
+template <int H>
+__device__ void select_topk(const Ctx &x, int Ncur) {
+    using Lt = Layout<H>;
+    constexpr int NW = H / 32, NCH = Lt::NCH;
+    if (x.wg != 0) return;
+    const int g = x.g, lane = x.lane;
+    const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
+    const float *part = (const float *)(x.smem + Lt::PART_OFF) + g * NW * KT;
+    uint32_t *km = (uint32_t *)(x.smem + Lt::KM_OFF) + g * 16;
+    int *newlist = (int *)(x.smem + Lt::NEW_OFF) + g * KT;
+    int *nnew_slot = (int *)(x.smem + Lt::MISC_OFF + 16) + g;
+    const int C = Ncur + H;
+    uint32_t key[NCH];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = 32 * k + lane;
+        float v = 0.f;
+        if (c < Ncur) {
+            for (int w = 0; w < NW; ++w) v += part[w * KT + c];
+        } else if (c < C) {
+            v = score[c];
+        }
+        key[k] = (32 * k + lane < C) ? __float_as_uint(v) >> 16 : 0u;  // invalid candidates: key 0, never kept below
+    }
+    uint32_t T = 0u;
+    {
+        uint32_t nz = 0u;
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) nz += key[k] != 0u ? 1u : 0u;
+        if (__reduce_add_sync(0xffffffffu, nz) > (uint32_t)KT) {
+            // bits 15..0 of the key (bit 15, the sign, is 0): steps at bits 14, 12, .., 0
+#pragma unroll 1
+            for (int b = 14; b >= 0; b -= 2) {
+                const uint32_t c1 = T | (1u << b), c2 = T | (2u << b), c3 = T | (3u << b);
+                uint32_t n1 = 0u, n2 = 0u, n3 = 0u;
+#pragma unroll
+                for (int k = 0; k < NCH; ++k) {
+                    n1 += key[k] >= c1 ? 1u : 0u;
+                    n2 += key[k] >= c2 ? 1u : 0u;
+                    n3 += key[k] >= c3 ? 1u : 0u;
+                }
+                n1 = __reduce_add_sync(0xffffffffu, n1);
+                n2 = __reduce_add_sync(0xffffffffu, n2);
+                n3 = __reduce_add_sync(0xffffffffu, n3);
+                T = n3 >= (uint32_t)KT ? c3 : (n2 >= (uint32_t)KT ? c2 : (n1 >= (uint32_t)KT ? c1 : T));
+            }
+        }
+    }
+    uint32_t gt = 0u;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) gt += key[k] > T ? 1u : 0u;
+    const int need = KT - (int)__reduce_add_sync(0xffffffffu, gt);  // ties at T to keep
+    const unsigned below = (1u << lane) - 1u;
+    int base = 0, eqb = 0, nb = 0;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) {
+        const int c = 32 * k + lane;
+        const bool valid = c < C;
+        const bool eq = valid && key[k] == T;
+        const unsigned meq = __ballot_sync(0xffffffffu, eq);
+        const bool kp = key[k] > T || (eq && eqb + __popc(meq & below) < need);
+        const unsigned m = __ballot_sync(0xffffffffu, kp);
+        const unsigned mnew = m & __ballot_sync(0xffffffffu, valid && c >= Ncur);
+        if (lane == 0) km[k] = m;
+        if (kp && c >= Ncur) newlist[nb + __popc(mnew & below)] = (base + __popc(m & below)) | ((c - Ncur) << 16);
+        base += __popc(m);
+        eqb += __popc(meq);
+        nb += __popc(mnew);
+    }
+    if (lane == 0) *nnew_slot = nb;
+}
+
+// Kept flag of candidate c of the group's box (after select_topk and a group_sync).
+template <int H> __device__ __forceinline__ bool cand_kept(const Ctx &x, int c) {
+    using Lt = Layout<H>;
+    const uint32_t *km = (const uint32_t *)(x.smem + Lt::KM_OFF) + x.g * 16;
+    return (km[c >> 5] >> (c & 31)) & 1u;
+}
+
+// Operand rows of the kept new symbols (positions KT - nnew .. KT - 1 of the
+// group's box): one-hot columns, the neuron's magnitude ga (read back from
+// the candidate scores) at its own entry and zeros elsewhere, written as
+// 16-byte chunks of eight neurons.
+template <int H, bool SOUND>
+__device__ __forceinline__ void fill_new_rows(const Ctx &x, int Ncur) {
+    using Lt = Layout<H>;
+    const int g = x.g, i = x.i;
+    const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
+    const int *newlist = (const int *)(x.smem + Lt::NEW_OFF) + g * KT;
+    const int nnew = ((const int *)(x.smem + Lt::MISC_OFF + 16))[g];
+    constexpr int CH = H / 8;  // 16-byte chunks per row
+    for (int e = i; e < nnew * CH; e += H) {
+        const int q = e / CH, ch = e - q * CH;
+        const int ent = newlist[q];
+        const uint32_t row = (uint32_t)(g * KT + (ent & 0xffff));
+        const int neuron = ent >> 16;
+        uint32_t val = 0u;
+        const int el = neuron & 7;
+        if ((neuron >> 3) == ch) {
+            const float ga = score[Ncur + neuron];
+            const __nv_bfloat16 b = SOUND ? __float2bfloat16_ru(ga) : __float2bfloat16_rn(ga);
+            const uint32_t bits = (uint32_t)__bfloat16_as_ushort(b);
+            val = (el & 1) ? (bits << 16) : bits;
+        }
+        const int wi = el >> 1;
+        unsigned char *XA = x.smem + Lt::XA_OFF + (ch >> 3) * Lt::XA_SLICE;
+        const uint32_t c16 = (uint32_t)(ch & 7);
+        *(uint4 *)(XA + row * 128u + ((c16 ^ (row & 7u)) << 4)) =
+            make_uint4(wi == 0 ? val : 0u, wi == 1 ? val : 0u, wi == 2 ? val : 0u, wi == 3 ? val : 0u);
+    }
+}
+
+// Center (as a BF16 hi/lo pair, operand chunk XC), independent part and the
+// sound operand vector v = rho1 |operand| + x_r of neuron n of the group's
+// box, for the next layer's MMA and |W_b| v pass.
+template <int H, bool SOUND>
+__device__ __forceinline__ void store_neuron(const Ctx &x, const TcParams &p, int n, float c2, float xi, float mag) {
+    using Lt = Layout<H>;
+    const int g = x.g;
+    const uint32_t kk = (uint32_t)(n & 63);
+    const __nv_bfloat16 chi = __float2bfloat16_rn(c2);
+    const float rem = c2 - __bfloat162float(chi);
+    const __nv_bfloat16 clo = __float2bfloat16_rn(rem);
+    const float rc = rem - __bfloat162float(clo);  // exact in fp32
+    unsigned char *XC = x.smem + Lt::XC_OFF + (n >> 6) * Lt::XC_SLICE;
+    *(__nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g), kk)) = chi;
+    *(__nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g + 1), kk)) = clo;
+    const float xr = SOUND ? ru_add(xi, fabsf(rc)) : xi;
+    ((float *)(x.smem + Lt::XR_OFF))[g * H + n] = xr;
+    if (SOUND) {
+        const float m2 = ru_add(ru_add(mag, fabsf(__bfloat162float(chi))), fabsf(__bfloat162float(clo)));
+        ((float *)(x.smem + Lt::V_OFF))[g * H + n] = ru_fma(p.rho1, m2, xr);
+    } else {
+        ((float *)(x.smem + Lt::V_OFF))[g * H + n] = xr;
+    }
+}
+
+// First layer (3 -> H, SIMT): thread i holds neuron i's three noise entries
+// a0 (already scaled by its slope al); truncation over 3 old + H new
+// candidates; operand rows written element-wise.
+template <int H, bool SOUND>
+__device__ void first_layer_store(const Ctx &x, const TcParams &p, const float (&a0)[3], float sa, float al,
+                                  float ga, float c2, float xi) {
     using Lt = Layout<H>;
     const int g = x.g, i = x.i, lane = x.lane, wg = x.wg;
     float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
-    uint8_t *keep = x.smem + Lt::KEEP_OFF + g * Lt::NCAND;
-    short *pos = (short *)(x.smem + Lt::POS_OFF) + g * Lt::NCAND;
-    int *newlist = (int *)(x.smem + Lt::NEW_OFF) + g * KT;
-    int *hist = (int *)(x.smem + Lt::HIST_OFF) + g * 256;
-    int *nnew_slot = (int *)(x.smem + Lt::MISC_OFF + 16) + g;
-    uint32_t *sel = (uint32_t *)(x.smem + Lt::MISC_OFF + 32) + 2 * g;  // [0] prefix, [1] need
-    const int C = Ncur + H;
-    // column L1 norms of the old columns over the H neurons: butterfly
-    // reduce-scatter inside the warp (lane l ends with 2 column sums); a is
-    // consumed here
 #pragma unroll
-    for (int k = 0; k < KT; ++k) a[k] = fabsf(a[k]);
+    for (int k = 0; k < 3; ++k) {
+        const float s = warp_sum_f(fabsf(a0[k]));
+        if (lane == 0) part[wg * KT + k] = s;
+    }
+    score[3 + i] = ga;
+    group_sync(g, H);
+    select_topk<H>(x, 3);
+    group_sync(g, H);
+    const uint32_t km0 = ((const uint32_t *)(x.smem + Lt::KM_OFF))[g * 16];
+    unsigned char *XA = x.smem + Lt::XA_OFF + (i >> 6) * Lt::XA_SLICE;
+    const uint32_t kk = (uint32_t)(i & 63);
+    float dropped = 0.f;
 #pragma unroll
-    for (int half = KT / 2, o = 16; o >= 1; half >>= 1, o >>= 1) {
+    for (int k = 0; k < 3; ++k) {
+        if (!((km0 >> k) & 1u)) {
+            dropped = ru_add(dropped, fabsf(a0[k]));
+        } else {
+            const int pp = __popc(km0 & ((1u << k) - 1u));
+            *(__nv_bfloat16 *)(XA + ptx::sw128_offset((uint32_t)(g * KT + pp), kk)) = __float2bfloat16_rn(a0[k]);
+        }
+    }
+    if (!cand_kept<H>(x, 3 + i)) dropped = ru_add(dropped, ga);
+    fill_new_rows<H, SOUND>(x, 3);
+    store_neuron<H, SOUND>(x, p, i, c2, ru_add(xi, dropped), SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
+}
+
+// Sum of 16 non-negative values, rounded up, as a balanced tree.
+__device__ __forceinline__ float ru_sum16(const float (&t)[16]) {
+    float u[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) u[k] = ru_add(t[2 * k], t[2 * k + 1]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = ru_add(u[2 * k], u[2 * k + 1]);
+    return ru_add(ru_add(u[0], u[1]), ru_add(u[2], u[3]));
+}
+
+// Epilogue of one hidden layer for the group's box. Warp wg holds neurons
+// 32 wg .. 32 wg + 31 in the accumulator fragment layout: for half h, lane t
+// has neurons nA = 32 wg + 16 h + t/4 and nB = nA + 8 at noise columns
+// 8 j + 2(t%4) + e (j < 8, e < 2), a[h][j][2 AB + e] with AB = 0 for nA and
+// 1 for nB. The four lanes of a quad share their neurons; per-neuron scalars
+// are computed redundantly in the quad (bit-identical), and lane t%4 == slot
+// stores slot `2h + AB`. Column norms reduce-scatter across the lanes; kept
+// columns go to operand B by transposing stmatrix (row = position, 16 bytes
+// = eight consecutive neurons).
+template <int H, bool SOUND>
+__device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, int col0, float c_n, float xinf_n) {
+    using Lt = Layout<H>;
+    const int g = x.g, lane = x.lane, wg = x.wg;
+    float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
+    float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
+    const int quad = lane >> 2, qi = lane & 3;
+    float a[2][8][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) ptx::tmem_ld16x256_x8(tl + ((uint32_t)(16 * h) << 16) + (uint32_t)col0, &a[h][0][0]);
+    float cs[4], xs[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int src = 16 * (s >> 1) + 8 * (s & 1) + quad;
+        cs[s] = __shfl_sync(0xffffffffu, c_n, src);
+        xs[s] = __shfl_sync(0xffffffffu, xinf_n, src);
+    }
+    ptx::tmem_wait_ld();
+    // range: noise magnitudes per neuron, summed over the quad (rounded up)
+    float sa[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int h = s >> 1, q0 = 2 * (s & 1);
+        float t[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            t[2 * j] = fabsf(a[h][j][q0]);
+            t[2 * j + 1] = fabsf(a[h][j][q0 + 1]);
+        }
+        float v = ru_sum16(t);
+        v = ru_add(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        v = ru_add(v, __shfl_xor_sync(0xffffffffu, v, 2));
+        sa[s] = v;
+    }
+    float al[4], ga[4], c2[4], xi[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) relu_rule<SOUND>(sa[s], cs[s], xs[s], p.ub2u, al[s], ga[s], c2[s], xi[s]);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (qi == s) score[KT + 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad] = ga[s];
+    // scale; column L1 norms over the warp's 32 neurons (reduce-scatter: lane
+    // t ends with symbols 8(t/4) + 2(t%4) + k, k < 2)
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            a[0][j][q] *= al[q >> 1];
+            a[1][j][q] *= al[2 + (q >> 1)];
+        }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+        for (int e = 0; e < 2; ++e)
+            v[2 * j + e] = (fabsf(a[0][j][e]) + fabsf(a[0][j][2 + e])) + (fabsf(a[1][j][e]) + fabsf(a[1][j][2 + e]));
+#pragma unroll
+    for (int half = 8, o = 16; o >= 4; half >>= 1, o >>= 1) {
         const bool up = (lane & o) != 0;
 #pragma unroll
         for (int k = 0; k < half; ++k) {
-            const float send = up ? a[k] : a[k + half];
-            const float keepv = up ? a[k + half] : a[k];
-            a[k] = keepv + __shfl_xor_sync(0xffffffffu, send, o);
+            const float send = up ? v[k] : v[k + half];
+            const float keepv = up ? v[k + half] : v[k];
+            v[k] = keepv + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
+    part[wg * KT + 8 * quad + 2 * qi] = v[0];
+    part[wg * KT + 8 * quad + 2 * qi + 1] = v[1];
+    group_sync(g, H);
+    select_topk<H>(x, KT);
+    group_sync(g, H);
+    const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * 16;
+    const unsigned long long kept = ((unsigned long long)kmw[1] << 32) | kmw[0];
+    // dropped magnitudes per neuron (quad-summed, rounded up) to x_inf
     {
-        const int col = ((lane & 16) ? 32 : 0) + ((lane & 8) ? 16 : 0) + ((lane & 4) ? 8 : 0) +
-                        ((lane & 2) ? 4 : 0) + ((lane & 1) ? 2 : 0);
-        part[wg * KT + col] = a[0];
-        part[wg * KT + col + 1] = a[1];
-    }
-    score[Ncur + i] = gamma;  // the new symbol of neuron i (one nonzero entry)
-    if (i == 0) { sel[0] = 0u; sel[1] = KT; }
-    group_sync(g, H);
-    if (i < Ncur) {
-        float v = 0.f;
-        for (int w = 0; w < H / 32; ++w) v += part[w * KT + i];
-        score[i] = v;
-    }
-    // exact top-KT by radix select on the score bits (non-negative floats
-    // order like their bit patterns), 8 bits per pass
-    uint32_t pmask = 0u;
-#pragma unroll 1
-    for (int shift = 24; shift >= 0; shift -= 8) {
-        for (int e = i; e < 256; e += H) hist[e] = 0;
-        group_sync(g, H);
-        const uint32_t prefix = sel[0];
-        for (int c = i; c < C; c += H) {
-            const uint32_t key = __float_as_uint(score[c]);
-            if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1);
-        }
-        group_sync(g, H);
-        if (wg == 0) {
-            // lane l owns digits 255-8l .. 248-8l (descending)
-            int cnt[8], tot = 0;
+        const unsigned long long mine = ~kept >> (2 * qi);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) { cnt[q] = hist[255 - 8 * lane - q]; tot += cnt[q]; }
-            int incl = tot;
+        for (int s = 0; s < 4; ++s) {
+            const int h = s >> 1, q0 = 2 * (s & 1);
+            float t[16];
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const int need = (int)sel[1];
-            const unsigned hit = __ballot_sync(0xffffffffu, incl >= need);
-            const int L = __ffs(hit) - 1;
-            if (lane == L) {
-                int above = incl - tot, d = 255 - 8 * lane;
+            for (int j = 0; j < 8; ++j)
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (above + cnt[q] >= need) { d = 255 - 8 * lane - q; break; }
-                    above += cnt[q];
-                }
-                sel[0] = prefix | ((uint32_t)d << shift);
-                sel[1] = (uint32_t)(need - above);
-            }
+                for (int e = 0; e < 2; ++e) t[2 * j + e] = ((mine >> (8 * j + e)) & 1ull) ? fabsf(a[h][j][q0 + e]) : 0.f;
+            float d = ru_sum16(t);
+            d = ru_add(d, __shfl_xor_sync(0xffffffffu, d, 1));
+            d = ru_add(d, __shfl_xor_sync(0xffffffffu, d, 2));
+            xi[s] = ru_add(xi[s], d);
         }
-        pmask |= 255u << shift;
-        group_sync(g, H);
     }
-    if (wg == 0) {  // keep flags, positions, kept new symbols, in candidate order
-        const uint32_t T = sel[0];
-        int take_eq = (int)sel[1];
-        const unsigned below = (1u << lane) - 1u;
-        int base = 0;
-        for (int c0 = 0; c0 < C; c0 += 32) {
-            const int c = c0 + lane;
-            const uint32_t key = (c < C) ? __float_as_uint(score[c]) : 0u;
-            const bool gt = (c < C) && key > T, eq = (c < C) && key == T;
-            const unsigned meq = __ballot_sync(0xffffffffu, eq);
-            const bool k = gt || (eq && __popc(meq & below) < take_eq);
-            take_eq -= min(__popc(meq), max(take_eq, 0));
-            const unsigned m = __ballot_sync(0xffffffffu, k);
-            if (c < C) {
-                keep[c] = k;
-                pos[c] = k ? (short)(base + __popc(m & below)) : (short)-1;
-            }
-            base += __popc(m);
-        }
-        __syncwarp();
-        int cnt = 0;  // kept new symbols as (position, neuron)
-        for (int c0 = Ncur; c0 < C; c0 += 32) {
-            const int c = c0 + lane;
-            const bool k = (c < C) && keep[c];
-            const unsigned m = __ballot_sync(0xffffffffu, k);
-            if (k) newlist[cnt + __popc(m & below)] = (int)pos[c] | ((c - Ncur) << 16);
-            cnt += __popc(m);
-        }
-        if (lane == 0) *nnew_slot = cnt;
-    }
-    reload(a);  // the scaled old columns again (overlaps the warp-0 listing)
-    group_sync(g, H);
-    const int nnew = *nnew_slot;
-    // dropped magnitudes to x_inf; kept values to operand B (row n = g*KT + pos)
-    unsigned char *XA = x.smem + Lt::XA_OFF + (i >> 6) * Lt::XA_SLICE;
-    const uint32_t kk = (uint32_t)(i & 63);
-    float dropped = 0.f, arow = 0.f;
+    // kept old columns -> operand B rows g*KT + pos (dropped rows to a dummy area)
+    {
+        const int mi = lane >> 3, r = lane & 7;
+        const int nb = 32 * wg + 8 * mi;
+        const uint32_t xa = ptx::smem_u32(x.smem + Lt::XA_OFF + (nb >> 6) * Lt::XA_SLICE);
+        const uint32_t c16 = (uint32_t)((nb & 63) >> 3);
+        const uint32_t dummy = ptx::smem_u32(x.smem + Lt::DUMMY_OFF) + 16u * (uint32_t)lane;
 #pragma unroll
-    for (int k = 0; k < KT; ++k) {
-        if (k < Ncur) {
-            const int pp = pos[k];
-            if (pp < 0) {
-                dropped = ru_add(dropped, fabsf(a[k]));
-            } else {
-                const __nv_bfloat16 v = __float2bfloat16_rn(a[k]);
-                *(__nv_bfloat16 *)(XA + ptx::sw128_offset((uint32_t)(g * KT + pp), kk)) = v;
-                arow = ru_add(arow, fabsf(__bfloat162float(v)));
+        for (int j = 0; j < 8; ++j) {
+            const int sym = 8 * j + r;
+            const bool k = (kept >> sym) & 1ull;
+            const uint32_t row = (uint32_t)(g * KT + __popcll(kept & ((1ull << sym) - 1ull)));
+            const uint32_t addr = k ? xa + row * 128u + ((c16 ^ (row & 7u)) << 4) : dummy;
+            uint32_t R[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const __nv_bfloat162 b = __floats2bfloat162_rn(a[m >> 1][j][2 * (m & 1)], a[m >> 1][j][2 * (m & 1) + 1]);
+                R[m] = *(const uint32_t *)&b;
             }
+            ptx::stmatrix_x4_trans(addr, R[0], R[1], R[2], R[3]);
         }
     }
-    if (pos[Ncur + i] < 0) dropped = ru_add(dropped, gamma);
-    for (int q = 0; q < nnew; ++q) {
-        const int e = newlist[q];
-        const int pp = e & 0xffff, neuron = e >> 16;
-        float v = 0.f;
-        if (neuron == i) {
-            v = SOUND ? bf16_ru(gamma) : __bfloat162float(__float2bfloat16_rn(gamma));
-            arow = ru_add(arow, v);
-        }
-        *(__nv_bfloat16 *)(XA + ptx::sw128_offset((uint32_t)(g * KT + pp), kk)) = __float2bfloat16_rn(v);
-    }
-    xinf = ru_add(xinf, dropped);
-    // center as a bf16 hi/lo pair; the residual is exact in fp32
-    const __nv_bfloat16 chi = __float2bfloat16_rn(c2);
-    const float rem = c2 - __bfloat162float(chi);
-    const __nv_bfloat16 clo = __float2bfloat16_rn(rem);
-    const float rc = rem - __bfloat162float(clo);
-    unsigned char *XC = x.smem + Lt::XC_OFF + (i >> 6) * Lt::XC_SLICE;
-    *(__nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g), kk)) = chi;
-    *(__nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g + 1), kk)) = clo;
-    const float xr = SOUND ? ru_add(xinf, fabsf(rc)) : xinf;
-    ((float *)(x.smem + Lt::XR_OFF))[g * H + i] = xr;
-    if (SOUND) {
-        const float mag = ru_add(ru_add(arow, fabsf(__bfloat162float(chi))), fabsf(__bfloat162float(clo)));
-        ((float *)(x.smem + Lt::V_OFF))[g * H + i] = ru_fma(p.rho1, mag, xr);
-    } else {
-        ((float *)(x.smem + Lt::V_OFF))[g * H + i] = xr;
-    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (!cand_kept<H>(x, KT + 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad)) xi[s] = ru_add(xi[s], ga[s]);
+    fill_new_rows<H, SOUND>(x, KT);
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+        if (qi == s)
+            store_neuron<H, SOUND>(x, p, 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad, c2[s], xi[s],
+                                   SOUND ? operand_mag_bound(al[s], sa[s], ga[s]) : 0.f);
 }
 
 template <int H, bool SOUND>
@@ -324,9 +508,12 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
         ptx::mbar_init(&x.bars[4], 1);
         ptx::fence_mbar_init();
         *x.abort_flag = 0;
+        uint32_t *sel = (uint32_t *)(x.smem + Lt::MISC_OFF + 32);
+        for (int gg = 0; gg < NB; ++gg) { sel[2 * gg] = 0u; sel[2 * gg + 1] = KT; }
     }
     // zero the center chunk once (rows beyond 2*NB stay zero); output weights to smem
-    for (int e = tid; e < Lt::S * Lt::XC_SLICE / 4; e += NT) ((uint32_t *)(x.smem + Lt::XC_OFF))[e] = 0u;
+    for (int e = tid; e < Lt::S * NCC * 32; e += NT)
+        ((uint32_t *)(x.smem + Lt::XC_OFF + (e / (NCC * 32)) * Lt::XC_SLICE))[e % (NCC * 32)] = 0u;
     float *wout = (float *)(x.smem + Lt::WOUT_OFF);
     for (int e = tid; e < H; e += NT) wout[e] = p.wout[e];
     if (warp == 0) ptx::tmem_alloc(tmem_slot, 512);
@@ -339,6 +526,33 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     const long long n = src.n;
     const long long ntiles = (n + NB - 1) / NB;
     uint32_t gring = 0, accn = 0;
+    // weight K slices stream through the ring in one global order (layer 1..L-2
+    // of every tile this CTA takes); thread 0 issues them up to two ahead of
+    // the consumers, across layer and tile boundaries, and never past the
+    // CTA's last slice
+    const int NL = p.L - 2;
+    const long long my_tiles = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const uint32_t total_slices = (uint32_t)(my_tiles * NL * Lt::S);
+    uint32_t gload = 0;
+    int ld_layer = 1, ld_slice = 0;
+    auto issue_upto = [&](uint32_t target) {  // thread 0
+        while (gload < target && gload < total_slices && !*x.abort_flag) {
+            const uint32_t gg = gload, st = gg & 1u;
+            if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, kSpin)) { fail(x, p, 3); return; }
+            unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
+            ptx::mbar_arrive_expect_tx(&x.bars[st], Lt::STAGE);
+            const CUtensorMap *mb = &p.wb[ld_layer - 1], *mr = &p.wr[ld_layer - 1];
+            for (int m = 0; m < Lt::MT; ++m) {
+                ptx::tma_load_2d(base + m * Lt::TILE, mb, ld_slice * 64, m * 128, &x.bars[st]);
+                ptx::tma_load_2d(base + (Lt::MT + m) * Lt::TILE, mr, ld_slice * 64, m * 128, &x.bars[st]);
+            }
+            ++gload;
+            if (++ld_slice == Lt::S) {
+                ld_slice = 0;
+                if (++ld_layer > NL) ld_layer = 1;
+            }
+        }
+    };
 
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         if (*x.abort_flag) break;
@@ -362,34 +576,28 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
         group_sync(g, H);
         // ---- first layer (3 -> H) on the SIMT cores ----------------------------
         {
-            float a[KT];
-#pragma unroll
-            for (int k = 0; k < KT; ++k) a[k] = 0.f;
             const float w0[3] = {p.W0[i * 3], p.W0[i * 3 + 1], p.W0[i * 3 + 2]};
             const float b0 = p.b[0][i];
-            const float hb[3] = {boxf[g * 8 + 3], boxf[g * 8 + 4], boxf[g * 8 + 5]};
+            float a0[3];
             float c = b0, cm = fabsf(b0), am = 0.f;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const float cd = boxf[g * 8 + d];
                 c = fmaf(w0[d], cd, c);
                 cm = ru_fma(fabsf(w0[d]), fabsf(cd), cm);
-                a[d] = w0[d] * hb[d];
-                am = ru_add(am, fabsf(a[d]));
+                a0[d] = w0[d] * boxf[g * 8 + 3 + d];
+                am = ru_add(am, fabsf(a0[d]));
             }
             float xinf = 0.f;
             if (SOUND) {
                 xinf = ru_mul(cm, 2.3841858e-07f);  // 3-FMA sum: gamma_3 < 2^-22
                 xinf = ru_fma(am, 1.1920929e-07f, xinf);  // one rounding per product
             }
-            float c2, al, ga;
-            relu_apply<SOUND>(a, c, xinf, c2, al, ga, p.ub2u);
-            truncate_and_store<H, SOUND>(x, p, a, 3, ga, xinf, c2, [&](float (&r)[KT]) {
+            float al, ga, c2, xi;
+            relu_rule<SOUND>(am, c, xinf, p.ub2u, al, ga, c2, xi);
 #pragma unroll
-                for (int k = 0; k < KT; ++k) r[k] = 0.f;
-#pragma unroll
-                for (int d = 0; d < 3; ++d) r[d] = al * (w0[d] * hb[d]);
-            });
+            for (int d = 0; d < 3; ++d) a0[d] *= al;
+            first_layer_store<H, SOUND>(x, p, a0, am, al, ga, c2, xi);
         }
         // ---- hidden layers on the tensor cores ---------------------------------
         for (int l = 1; l + 1 < p.L; ++l) {
@@ -397,23 +605,9 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             ptx::tc_fence_before();    // previous TMEM reads done before new MMAs
             __syncthreads();
             if (*x.abort_flag) break;
-            float xacc = 0.f;
-            const CUtensorMap *mb = &p.wb[l - 1], *mr = &p.wr[l - 1];
+            float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;  // rounded-up |W_b| v partials, boxes 0 and 1
             const uint32_t g0 = gring;
-            auto load_slice = [&](int s) {  // thread 0
-                const uint32_t gg = g0 + (uint32_t)s, st = gg & 1u;
-                if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, kSpin)) { fail(x, p, 3); return; }
-                unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
-                ptx::mbar_arrive_expect_tx(&x.bars[st], Lt::STAGE);
-                for (int m = 0; m < Lt::MT; ++m) {
-                    ptx::tma_load_2d(base + m * Lt::TILE, mb, s * 64, m * 128, &x.bars[st]);
-                    ptx::tma_load_2d(base + (Lt::MT + m) * Lt::TILE, mr, s * 64, m * 128, &x.bars[st]);
-                }
-            };
-            if (tid == 0) {
-                load_slice(0);
-                if (Lt::S > 1) load_slice(1);
-            }
+            if (tid == 0) issue_upto(g0 + 2);  // no-op when prefetched during the last epilogue
             const float *vg = (const float *)(x.smem + Lt::V_OFF) + g * H;
             for (int s = 0; s < Lt::S; ++s) {
                 const uint32_t gg = g0 + (uint32_t)s, st = gg & 1u, par = (gg >> 1) & 1u;
@@ -421,63 +615,69 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
                 if (tid == 0 && !*x.abort_flag) {
                     ptx::tc_fence_after();
-                    const uint32_t ia = ptx::idesc_bf16(128, NA), ic = ptx::idesc_bf16(128, NCC);
+                    const uint32_t ia = ptx::idesc_bf16(128, NA + NCC);
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint32_t acc = (s | ks) ? 1u : 0u;
                         const uint64_t bA =
                             ptx::desc_kmajor_sw128(ptx::smem_u32(x.smem + Lt::XA_OFF + s * Lt::XA_SLICE)) + 2 * ks;
-                        const uint64_t bC =
-                            ptx::desc_kmajor_sw128(ptx::smem_u32(x.smem + Lt::XC_OFF + s * Lt::XC_SLICE)) + 2 * ks;
                         for (int m = 0; m < Lt::MT; ++m) {
                             const uint64_t aB = ptx::desc_kmajor_sw128(ptx::smem_u32(base + m * Lt::TILE)) + 2 * ks;
                             const uint64_t aR =
                                 ptx::desc_kmajor_sw128(ptx::smem_u32(base + (Lt::MT + m) * Lt::TILE)) + 2 * ks;
-                            ptx::mma_bf16(x.tmem + m * NA, aB, bA, ia, acc);
-                            ptx::mma_bf16(x.tmem + m * NA, aR, bA, ia, 1u);
-                            ptx::mma_bf16(x.tmem + Lt::MT * NA + m * NCC, aB, bC, ic, acc);
-                            ptx::mma_bf16(x.tmem + Lt::MT * NA + m * NCC, aR, bC, ic, 1u);
+                            ptx::mma_bf16(x.tmem + m * TM_STRIDE, aB, bA, ia, acc);
+                            ptx::mma_bf16(x.tmem + m * TM_STRIDE, aR, bA, ia, 1u);
                         }
                     }
                     ptx::mma_commit(&x.bars[2 + st]);
                     if (s + 1 == Lt::S) ptx::mma_commit(&x.bars[4]);
                 }
-                // x_inf' += |W_b| v of the group's box from the resident slice
+                // x_inf' += |W_b| v from the resident slice: thread (g, i) takes
+                // row i over inputs 32 g .. 32 g + 31 of the slice for both boxes
+                // (one read and unpack of each weight, paired FMAs)
                 {
                     const int r = i & 127;
                     const unsigned char *row = base + m_of_thread * Lt::TILE + r * 128;
+                    const float *v0 = (const float *)(x.smem + Lt::V_OFF) + s * 64;
+                    const float *v1 = v0 + H;
 #pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int ch = 4 * g + cc;
                         const uint4 q = *(const uint4 *)(row + (((ch ^ (r & 7)) & 7) << 4));
-                        const __nv_bfloat162 *w2 = (const __nv_bfloat162 *)&q;
-                        const float4 va = *(const float4 *)(vg + s * 64 + ch * 8);
-                        const float4 vb = *(const float4 *)(vg + s * 64 + ch * 8 + 4);
-                        const float vv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+                        const float4 a0 = *(const float4 *)(v0 + ch * 8), a1 = *(const float4 *)(v0 + ch * 8 + 4);
+                        const float4 b0 = *(const float4 *)(v1 + ch * 8), b1 = *(const float4 *)(v1 + ch * 8 + 4);
+                        const uint32_t wq[4] = {q.x, q.y, q.z, q.w};
+                        const float va[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        const float vb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
                         for (int e2 = 0; e2 < 4; ++e2) {
-                            const float2 wf = __bfloat1622float2(w2[e2]);
-                            xacc = ru_fma(fabsf(wf.x), vv[2 * e2], xacc);
-                            xacc = ru_fma(fabsf(wf.y), vv[2 * e2 + 1], xacc);
+                            // |w| of the pair as floats (bf16 bits in the high half)
+                            const float wlo = __uint_as_float((wq[e2] & 0x7fffu) << 16);
+                            const float whi = __uint_as_float(wq[e2] & 0x7fff0000u);
+                            fma2_ru(xa0, xa1, wlo, whi, va[2 * e2], va[2 * e2 + 1]);
+                            fma2_ru(xb0, xb1, wlo, whi, vb[2 * e2], vb[2 * e2 + 1]);
                         }
                     }
                 }
                 __syncwarp();
                 if (x.lane == 0) ptx::mbar_arrive(&x.bars[2 + st]);
-                if (tid == 0 && s + 2 < Lt::S && !*x.abort_flag) load_slice(s + 2);
+                if (tid == 0) issue_upto(g0 + (uint32_t)s + 3);
             }
             gring = g0 + Lt::S;
             if (!ptx::mbar_wait(&x.bars[4], accn & 1u, kSpin)) fail(x, p, 5);
             accn++;
+            if (tid == 0) issue_upto(gring + 2);  // next layer's (or tile's) first slices, during the epilogue
+            // the other group's box: hand over this thread's half of its |W_b| v
+            float *xp = (float *)(x.smem + Lt::XP_OFF);
+            const float xown = ru_add(g == 0 ? xa0 : xb0, g == 0 ? xa1 : xb1);
+            xp[(1 - g) * H + i] = ru_add(g == 0 ? xb0 : xa0, g == 0 ? xb1 : xa1);
             ptx::tc_fence_after();
             __syncthreads();  // every operand read of this layer is done
             if (*x.abort_flag) break;
             // ---- epilogue of the group's box -------------------------------
+            const float xacc = ru_add(xown, xp[g * H + i]);
             const float bias = p.b[l][i];
-            const uint32_t colA = tl + m_of_thread * NA + g * KT;
-            float a[KT];
-#pragma unroll
-            for (int q = 0; q < KT / 16; ++q) ptx::tmem_ld16(colA + q * 16, a + q * 16);
             float cc[2];
-            ptx::tmem_ld2(tl + Lt::MT * NA + m_of_thread * NCC + 2 * g, cc);
+            ptx::tmem_ld2(tl + m_of_thread * TM_STRIDE + NA + 2 * g, cc);
             ptx::tmem_wait_ld();
             // center: D(c_hi) + D(c_lo) + bias, each add rounded once
             const float c = (cc[0] + cc[1]) + bias;
@@ -489,15 +689,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             } else {
                 xinf = xacc;
             }
-            float c2, al, ga;
-            relu_apply<SOUND>(a, c, xinf, c2, al, ga, p.ub2u);
-            truncate_and_store<H, SOUND>(x, p, a, KT, ga, xinf, c2, [&](float (&r)[KT]) {
-#pragma unroll
-                for (int q = 0; q < KT / 16; ++q) ptx::tmem_ld16(colA + q * 16, r + q * 16);
-                ptx::tmem_wait_ld();
-#pragma unroll
-                for (int k = 0; k < KT; ++k) r[k] = al * r[k];
-            });
+            hidden_epilogue<H, SOUND>(x, p, tl, m_of_thread * TM_STRIDE + g * KT, c, xinf);
         }
         __syncthreads();
         if (*x.abort_flag) break;

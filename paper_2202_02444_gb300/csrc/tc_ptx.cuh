@@ -175,3 +175,52 @@ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {
 
 }  // namespace ptx
 }  // namespace sra
+
+namespace sra {
+namespace ptx {
+
+// 16 lanes x 256 bits (8 columns), one repetition: thread t receives lane
+// (base + t/4) columns 2(t%4), 2(t%4)+1 in v[0], v[1] and lane (base + 8 +
+// t/4) at the same columns in v[2], v[3] (the MMA accumulator fragment
+// layout). `taddr` carries the base lane in bits 31:16.
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float *v) {
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(taddr));
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
+    v[2] = __uint_as_float(r2);
+    v[3] = __uint_as_float(r3);
+}
+
+// Eight repetitions of the 16x256b load: columns 8j .. 8j+7 land in
+// v[4j .. 4j+3] with the layout of tmem_ld16x256.
+__device__ __forceinline__ void tmem_ld16x256_x8(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// Four 8x8 b16 matrices stored transposed: register r[m] of thread t holds
+// elements (row t/4, columns 2(t%4), 2(t%4)+1) of matrix m (low half first);
+// memory row k of matrix m (16 bytes at the address thread 8m + k supplies)
+// receives column k of that matrix.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t saddr, uint32_t r0, uint32_t r1, uint32_t r2,
+                                                  uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};" ::"r"(saddr), "r"(r0),
+                 "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
+
+}  // namespace ptx
+}  // namespace sra
