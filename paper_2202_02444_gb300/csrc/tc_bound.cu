@@ -130,8 +130,9 @@ __device__ __forceinline__ void relu_rule(float sa, float c, float xinf, float u
     else if (lo >= 0.f) { al = 1.f; be = 0.f; ga = 0.f; }
     else {
         // any slope in [0,1] is valid: g(x) = ReLU(x) - al x ranges over
-        // [0, max(-al lo, hi (1 - al))] on [lo, hi]
-        al = fminf(fmaxf(hi / (hi - lo), 0.f), 1.f);
+        // [0, max(-al lo, hi (1 - al))] on [lo, hi], so the Chebyshev slope
+        // hi / (hi - lo) may be approximate (fast division)
+        al = fminf(fmaxf(__fdividef(hi, hi - lo), 0.f), 1.f);
         const float m1 = __fmul_ru(al, -lo);
         const float m2 = __fmul_ru(hi, __fadd_ru(1.f, -al));
         const float M = fmaxf(m1, m2);
@@ -351,6 +352,18 @@ __device__ __forceinline__ float ru_sum16(const float (&t)[16]) {
     return ru_add(ru_add(u[0], u[1]), ru_add(u[2], u[3]));
 }
 
+// Reduce-scatter of four per-slot values over the four lanes of a quad,
+// rounded up: lane q of the quad returns the quad's sum of slot q.
+__device__ __forceinline__ float quad_scatter_ru(const float (&v)[4], int q) {
+    const bool hi2 = (q & 2) != 0;
+    const float k0 = hi2 ? v[2] : v[0], k1 = hi2 ? v[3] : v[1];
+    const float s0 = hi2 ? v[0] : v[2], s1 = hi2 ? v[1] : v[3];
+    const float r0 = ru_add(k0, __shfl_xor_sync(0xffffffffu, s0, 2));
+    const float r1 = ru_add(k1, __shfl_xor_sync(0xffffffffu, s1, 2));
+    const bool hi1 = (q & 1) != 0;
+    return ru_add(hi1 ? r1 : r0, __shfl_xor_sync(0xffffffffu, hi1 ? r0 : r1, 1));
+}
+
 // Epilogue of one hidden layer for the group's box. Warp wg holds neurons
 // 32 wg .. 32 wg + 31 in the accumulator fragment layout: for half h, lane t
 // has neurons nA = 32 wg + 16 h + t/4 and nB = nA + 8 at noise columns
@@ -370,36 +383,35 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     float a[2][8][4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) ptx::tmem_ld16x256_x8(tl + ((uint32_t)(16 * h) << 16) + (uint32_t)col0, &a[h][0][0]);
-    float cs[4], xs[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int src = 16 * (s >> 1) + 8 * (s & 1) + quad;
-        cs[s] = __shfl_sync(0xffffffffu, c_n, src);
-        xs[s] = __shfl_sync(0xffffffffu, xinf_n, src);
-    }
+    // lane t%4 == q computes the scalars of slot q (neuron nq)
+    const int nq = 32 * wg + 16 * (qi >> 1) + 8 * (qi & 1) + quad;
+    const float cq = __shfl_sync(0xffffffffu, c_n, nq & 31);
+    const float xq = __shfl_sync(0xffffffffu, xinf_n, nq & 31);
     ptx::tmem_wait_ld();
-    // range: noise magnitudes per neuron, summed over the quad (rounded up)
-    float sa[4];
+    // range: noise magnitudes per neuron, reduce-scattered over the quad
+    // (rounded up): lane q ends with slot q's sum
+    float sa;
+    {
+        float ps[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int h = s >> 1, q0 = 2 * (s & 1);
-        float t[16];
+        for (int s = 0; s < 4; ++s) {
+            const int h = s >> 1, q0 = 2 * (s & 1);
+            float t[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            t[2 * j] = fabsf(a[h][j][q0]);
-            t[2 * j + 1] = fabsf(a[h][j][q0 + 1]);
+            for (int j = 0; j < 8; ++j) {
+                t[2 * j] = fabsf(a[h][j][q0]);
+                t[2 * j + 1] = fabsf(a[h][j][q0 + 1]);
+            }
+            ps[s] = ru_sum16(t);
         }
-        float v = ru_sum16(t);
-        v = ru_add(v, __shfl_xor_sync(0xffffffffu, v, 1));
-        v = ru_add(v, __shfl_xor_sync(0xffffffffu, v, 2));
-        sa[s] = v;
+        sa = quad_scatter_ru(ps, qi);
     }
-    float al[4], ga[4], c2[4], xi[4];
+    float al, ga, c2, xi;
+    relu_rule<SOUND>(sa, cq, xq, p.ub2u, al, ga, c2, xi);
+    score[KT + nq] = ga;
+    float als[4];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) relu_rule<SOUND>(sa[s], cs[s], xs[s], p.ub2u, al[s], ga[s], c2[s], xi[s]);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-        if (qi == s) score[KT + 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad] = ga[s];
+    for (int s = 0; s < 4; ++s) als[s] = __shfl_sync(0xffffffffu, al, (lane & ~3) | s);
     // scale; column L1 norms over the warp's 32 neurons (reduce-scatter: lane
     // t ends with symbols 8(t/4) + 2(t%4) + k, k < 2)
     float v[16];
@@ -407,8 +419,8 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     for (int j = 0; j < 8; ++j)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            a[0][j][q] *= al[q >> 1];
-            a[1][j][q] *= al[2 + (q >> 1)];
+            a[0][j][q] *= als[q >> 1];
+            a[1][j][q] *= als[2 + (q >> 1)];
         }
 #pragma unroll
     for (int j = 0; j < 8; ++j)
@@ -432,22 +444,28 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     group_sync(g, H);
     const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * 16;
     const unsigned long long kept = ((unsigned long long)kmw[1] << 32) | kmw[0];
-    // dropped magnitudes per neuron (quad-summed, rounded up) to x_inf
+    // dropped magnitudes per neuron (reduce-scattered over the quad, rounded
+    // up) to x_inf: 0/1 masks times |a|, exact products
     {
         const unsigned long long mine = ~kept >> (2 * qi);
+        float mf[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) mf[2 * j + e] = ((mine >> (8 * j + e)) & 1ull) ? 1.f : 0.f;
+        float pd[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const int h = s >> 1, q0 = 2 * (s & 1);
-            float t[16];
+            float d0 = 0.f, d1 = 0.f;
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-#pragma unroll
-                for (int e = 0; e < 2; ++e) t[2 * j + e] = ((mine >> (8 * j + e)) & 1ull) ? fabsf(a[h][j][q0 + e]) : 0.f;
-            float d = ru_sum16(t);
-            d = ru_add(d, __shfl_xor_sync(0xffffffffu, d, 1));
-            d = ru_add(d, __shfl_xor_sync(0xffffffffu, d, 2));
-            xi[s] = ru_add(xi[s], d);
+            for (int j = 0; j < 8; ++j) {
+                d0 = ru_fma(mf[2 * j], fabsf(a[h][j][q0]), d0);
+                d1 = ru_fma(mf[2 * j + 1], fabsf(a[h][j][q0 + 1]), d1);
+            }
+            pd[s] = ru_add(d0, d1);
         }
+        xi = ru_add(xi, quad_scatter_ru(pd, qi));
     }
     // kept old columns -> operand B rows g*KT + pos (dropped rows to a dummy area)
     {
@@ -471,15 +489,9 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
             ptx::stmatrix_x4_trans(addr, R[0], R[1], R[2], R[3]);
         }
     }
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-        if (!cand_kept<H>(x, KT + 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad)) xi[s] = ru_add(xi[s], ga[s]);
+    if (!cand_kept<H>(x, KT + nq)) xi = ru_add(xi, ga);
     fill_new_rows<H, SOUND>(x, KT);
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-        if (qi == s)
-            store_neuron<H, SOUND>(x, p, 32 * wg + 16 * (s >> 1) + 8 * (s & 1) + quad, c2[s], xi[s],
-                                   SOUND ? operand_mag_bound(al[s], sa[s], ga[s]) : 0.f);
+    store_neuron<H, SOUND>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
 }
 
 template <int H, bool SOUND>
