@@ -51,6 +51,34 @@ def ray_iter_flops(mlp):
     return f
 
 
+# DRAM traffic of the dominant kernel's launch in the timed step, from one
+# ncu capture of this benchmark (dram__bytes_read.sum + dram__bytes_write.sum,
+# 1 pass, NVTX range timed_steps): reported only while the kernel's sources
+# are the ones captured (their SHA-1), else null.
+TRAFFIC = {
+    "tc_bound_kernel<256,true>": {"sha1": "22cf6170d6d53740c5b60adc943d9e75cb754399", "bytes": 3289600,
+                                  "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
+}
+TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
+                    "paper_2202_02444_gb300/csrc/tc_bound.h")
+
+
+def sources_sha1(paths):
+    import hashlib
+    h = hashlib.sha1()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel):
+    rec = TRAFFIC.get(kernel)
+    if not rec or rec["bytes"] is None or rec["sha1"] != sources_sha1(TC_BOUND_SOURCES):
+        return None
+    return rec["bytes"]
+
+
 def measured_peak(key, fallback):
     """A peak from the measured MEASURED_PEAKS.json (else the fallback)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -674,7 +702,9 @@ def main():
             "gpu_launches": args.steps * 5,
             "roofline": {"bound": bound, "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": captured_traffic("tc_bound_kernel<256,true>")
+                         if args.precision == "bf16_sound" else None,
                          "kernel_ms": mean_box, "kernel_ms_alone": kern_ms,
                          "timing": "CUDA events around each timed step (bound kernel + compaction)",
                          "flop_per_box": flop_box,
