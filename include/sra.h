@@ -51,7 +51,11 @@ enum {
     SRA_ARITH_INTERVAL = 0,
     SRA_ARITH_AFFINE_FIXED = 1,    /* keep only the input-domain symbols */
     SRA_ARITH_AFFINE_TRUNCATE = 2, /* keep the K largest symbols (column L1 norm) */
-    SRA_ARITH_AFFINE_FULL = 3      /* keep every symbol (small networks only) */
+    SRA_ARITH_AFFINE_FULL = 3      /* keep every symbol: up to 128 symbols on every kernel; past
+                                      that, box bounds (sra_bound_boxes, sra_classify_and_split and
+                                      the entry points built on them) of networks of width <= 64
+                                      without positional encoding whose state fits in shared memory
+                                      (e.g. 8-layer 32-wide: 227 symbols); else SRA_EUNSUPPORTED */
 };
 
 /* Slope of the activation linearisation: Chebyshev (App. A) or min-range. */

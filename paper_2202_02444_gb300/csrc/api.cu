@@ -219,9 +219,22 @@ void kd_tables(const float *lo, const float *hi, unsigned char n3[][3], unsigned
     }
 }
 
-// Launch RangeBound over a box source in FP32 or FP64 (SIMT engine).
+// Launch RangeBound over a box source in FP32 or FP64: the SIMT engine, or,
+// for affine-full past its 128 register columns, the shared-memory full
+// kernel (widths up to 64, no positional encoding).
 sra_status run_bound(const sra_net *n, const sra_opts *o, bool fp64, int s, const BoxSrc &src,
                      const BoundOut &out, long long n_hint, cudaStream_t st) {
+    if (o->arith == SRA_ARITH_AFFINE_FULL && s + n->new_syms > kKmaxList[sizeof kKmaxList / sizeof(int) - 1]) {
+        FullCfg fc;
+        if (n->pe || s != 3 || full_cfg(n->rows, s + n->new_syms, o->slope, fp64 ? 8 : 4, &fc) != SRA_OK)
+            return fail(SRA_EUNSUPPORTED,
+                        "affine-full with %d symbols needs the shared-memory full kernel: box bounds of a "
+                        "network without positional encoding, widths <= %d, state within shared memory",
+                        s + n->new_syms, kFullMaxWidth);
+        cudaError_t e = launch_full_bound(fp64, n->dev, src, out, fc, n_hint, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "full bound kernel launch: %s", cudaGetErrorString(e));
+        return SRA_OK;
+    }
     int kmax = 0;
     sra_status r = kmax_for(n, o, s, &kmax);
     if (r) return r;

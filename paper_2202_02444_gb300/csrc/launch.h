@@ -20,6 +20,19 @@ cudaError_t launch_bound_f32(int kmax, const NetDev &net, const BoxSrc &src, con
 cudaError_t launch_bound_f64(int kmax, const NetDev &net, const BoxSrc &src, const BoundOut &out,
                              const RangeCfg &cfg, long long grid, cudaStream_t st);
 
+// Affine-full RangeBound past the SIMT engine's register row: one CTA per
+// box, the noise matrix (rows x KS) in shared memory (full.cu).
+constexpr int kFullMaxWidth = 64;
+struct FullCfg {
+    int rows;   // state rows: the largest layer width
+    int KS;     // row stride: total symbols rounded up to 4
+    int slope;  // SRA_SLOPE_*
+    int x_off, w_off, smem;  // byte offsets and total dynamic shared memory
+};
+sra_status full_cfg(int rows, int total_syms, int slope, int tsize, FullCfg *fc);
+cudaError_t launch_full_bound(bool fp64, const NetDev &net, const BoxSrc &src, const BoundOut &out,
+                              const FullCfg &fc, long long n_hint, cudaStream_t st);
+
 struct RayParams;
 cudaError_t launch_rays_f32(int kmax, const NetDev &net, const void *rp, const RangeCfg &cfg,
                             int grid, cudaStream_t st);
