@@ -312,6 +312,49 @@ def batched_phase(sra, torch, cap):
             "wall_clock_note": "host-timed with synchronisation (one counter read per level)"}
 
 
+def policies_phase(sra, torch, dev):
+    """The range-analysis policies of Sec. 3 side by side on the paper's
+    8-layer 32-wide architecture (ReLU 3-[32]x7-1, He init, seed 41; the
+    trained shapes of its Table 1 are not available): 65,536 boxes with
+    half-widths log-uniform in [1/256, 1/20], FP32. Cost is reported per box
+    and relative to a plain forward evaluation of one point (sra_eval), the
+    normalisation of Table 1; width is the mean output range."""
+    mlp = wl.make_mlp([32] * 7, "relu", seed=41)
+    net = sra.Net(mlp)
+    B = 1 << 16
+    c, h = wl.make_boxes(B, seed=1, hw_lo=1 / 256, hw_hi=1 / 20)
+    C_, H_ = torch.from_numpy(c).to(dev), torch.from_numpy(h).to(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), r
+
+    ev_ms, _ = timed(lambda: sra.evaluate(net, C_))
+    res = {"workload": "ReLU 3-[32]x7-1 (He init, seed 41), 65,536 boxes, half-widths log-U[1/256, 1/20], FP32",
+           "forward_evals_per_s": B / (ev_ms / 1e3), "policies": {}}
+    for name, arith, K in (("interval", "interval", 0), ("affine-fixed", "fixed", 0),
+                           ("affine-truncate K=16", "truncate", 16), ("affine-truncate K=64", "truncate", 64),
+                           ("affine-full", "full", 0)):
+        o = sra.make_opts(arith=arith, K=K)
+        ms, (lo, hi, cl) = timed(lambda: sra.bound_boxes(net, C_, H_, opts=o))
+        res["policies"][name] = {"box_evals_per_s": B / (ms / 1e3), "cost_vs_forward": ms / ev_ms,
+                                 "mean_width": float((hi - lo).mean()),
+                                 "unknown_frac": float((cl == 0).float().mean())}
+    res["paper_table1_3d_cost_vs_forward"] = {"interval": 2.3, "affine-fixed": 6.7, "affine-truncate": 69.0,
+                                              "affine-full": 96.4, "hardware": "RTX 2070, JAX"}
+    net.close()
+    return res
+
+
 def make_frontier(sra, net, level, batch, opts):
     """Children of the UNKNOWN nodes at `level - 1` of the network's octree
     (the real frontier the level visits), tiled to `batch` nodes."""
@@ -647,6 +690,8 @@ def main():
                    "ms": sms, "queries_per_s": (1 << 16) / (sms / 1e3),
                    "decided_frac": float((rad > 0).float().mean()), "median_radius": float(rad.median())}
 
+    policies = policies_phase(sra, torch, dev) if rank == 0 else None
+
     batched = None
     if not args.no_batched and rank == 0:
         batched = batched_phase(sra, torch, args.batched_cap)
@@ -720,6 +765,7 @@ def main():
             "mesh": mesh,
             "empty_spheres": spheres,
             "frustum": frustum,
+            "policies": policies,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,
