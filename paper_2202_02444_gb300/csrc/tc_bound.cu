@@ -12,7 +12,9 @@
 //     chunk follows the noise rows of each K slice, so one MMA of N = 144
 //     covers both;
 //   * operand A: W as BF16 hi + lo (W = W_b + W_r + rho, |rho| <= u_b^2 |W|),
-//     streamed per 64-wide K slice by TMA into a two-stage ring;
+//     streamed per 64-wide K slice by TMA into a two-stage ring (lane 0 of
+//     the last warp issues the copies; lane 0 of warp m of group m issues
+//     the MMAs of M tile m, so no MMA issue waits on a refill);
 //   * D = (W_b + W_r) [X | c_hi c_lo] accumulates in TMEM (FP32);
 //   * x_inf' >= |W| v is accumulated by the SIMT threads from the resident
 //     W_b slice with round-up FMAs (|W| <= |W_b| / (1 - u_b));
@@ -86,16 +88,6 @@ __device__ __forceinline__ void group_sync(int g, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthreads) : "memory");
 }
 
-// (d0, d1) += (a0 * b0, a1 * b1), each rounded up (one paired FMA).
-__device__ __forceinline__ void fma2_ru(float &d0, float &d1, float a0, float a1, float b0, float b1) {
-    unsigned long long A, B, D;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(D) : "f"(d0), "f"(d1));
-    asm("fma.rp.f32x2 %0, %1, %2, %0;" : "+l"(D) : "l"(A), "l"(B));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(D));
-}
-
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -155,24 +147,27 @@ __device__ __forceinline__ float operand_mag_bound(float al, float sa, float ga)
     return ru_mul(ru_add(ru_mul(al, sa), ga), 1.0078125f);
 }
 
-// Top-KT of the group's Ncur + H candidates (Sec. 3.3 truncate), by warp 0
-// of the group alone. The old columns' scores (L1 norms) are summed from the
-// per-warp partials, the new symbols' magnitudes score[Ncur..) were written
-// by their neurons; the caller has synchronised the group after both. The
-// selection key is the score's top 16 bits (the BF16 truncation of a
-// non-negative float: the scores come from BF16 operands and carry their
+// Top-KT of the group's Ncur + H candidates (Sec. 3.3 truncate), by one
+// warp of the group: warp g of group g, so that the two groups' selections
+// run on different schedulers. The old columns' scores (L1 norms) are summed
+// from the per-warp partials, the new symbols' magnitudes score[Ncur..) were
+// written by their neurons; the caller has synchronised the group after
+// both. The selection key is the score's top 16 bits (the BF16 truncation of
+// a non-negative float: the scores come from BF16 operands and carry their
 // 2^-8 relative error, so lower bits are not significant); non-negative
-// floats order like their bit patterns. The KT-th largest key T is found by
-// bisection, two bits per step (three warp-wide counts), after a check
-// whether at most KT keys are non-zero (then T = 0). Ties at T go to the
-// lower candidate index, and kept columns stay in candidate order. Writes the kept mask of every chunk of 32 candidates,
-// the kept new symbols newlist[q] = position | neuron << 16 and nnew to
-// shared memory, valid after the caller's next group_sync.
+// floats order like their bit patterns. Unless at most KT keys are non-zero
+// (then T = 0), the KT-th largest key T is found by a four-way search (three
+// warp-wide counts per step) on an interval that starts at [the smallest
+// second-largest key of a lane, the largest key]. Ties at T go to the lower
+// candidate index, and kept columns stay in candidate order. Writes the kept
+// mask of every chunk of 32 candidates, the kept new symbols newlist[q] =
+// position | neuron << 16 and nnew to shared memory, valid after the
+// caller's next group_sync.
 template <int H>
 __device__ void select_topk(const Ctx &x, int Ncur) {
     using Lt = Layout<H>;
     constexpr int NW = H / 32, NCH = Lt::NCH;
-    if (x.wg != 0) return;
+    if (x.wg != x.g) return;  // warps 0 and H/32 + 1: different schedulers
     const int g = x.g, lane = x.lane;
     const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     const float *part = (const float *)(x.smem + Lt::PART_OFF) + g * NW * KT;
@@ -194,14 +189,21 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
     }
     uint32_t T = 0u;
     {
-        uint32_t nz = 0u;
+        uint32_t nz = 0u, m1 = 0u, m2 = 0u;  // the lane's two largest keys
 #pragma unroll
-        for (int k = 0; k < NCH; ++k) nz += key[k] != 0u ? 1u : 0u;
+        for (int k = 0; k < NCH; ++k) {
+            nz += key[k] != 0u ? 1u : 0u;
+            const uint32_t v = key[k];
+            m2 = v > m1 ? m1 : (v > m2 ? v : m2);
+            m1 = v > m1 ? v : m1;
+        }
         if (__reduce_add_sync(0xffffffffu, nz) > (uint32_t)KT) {
-            // bits 15..0 of the key (bit 15, the sign, is 0): steps at bits 14, 12, .., 0
-#pragma unroll 1
-            for (int b = 14; b >= 0; b -= 2) {
-                const uint32_t c1 = T | (1u << b), c2 = T | (2u << b), c3 = T | (3u << b);
+            // T is the largest key with at least KT keys >= T. Every lane holds
+            // two keys >= its m2, so 64 >= KT keys are >= lo; no key exceeds hi.
+            uint32_t lo = __reduce_min_sync(0xffffffffu, m2), hi = __reduce_max_sync(0xffffffffu, m1);
+            while (lo < hi) {  // invariant: count(>= lo) >= KT, count(> hi) < KT
+                const uint32_t w = hi - lo;  // split (lo, hi] at three points
+                const uint32_t c1 = lo + (w + 3u) / 4u, c2 = lo + (2u * w + 3u) / 4u, c3 = lo + (3u * w + 3u) / 4u;
                 uint32_t n1 = 0u, n2 = 0u, n3 = 0u;
 #pragma unroll
                 for (int k = 0; k < NCH; ++k) {
@@ -212,8 +214,12 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
                 n1 = __reduce_add_sync(0xffffffffu, n1);
                 n2 = __reduce_add_sync(0xffffffffu, n2);
                 n3 = __reduce_add_sync(0xffffffffu, n3);
-                T = n3 >= (uint32_t)KT ? c3 : (n2 >= (uint32_t)KT ? c2 : (n1 >= (uint32_t)KT ? c1 : T));
+                if (n3 >= (uint32_t)KT) lo = c3;
+                else if (n2 >= (uint32_t)KT) { lo = c2; hi = c3 - 1u; }
+                else if (n1 >= (uint32_t)KT) { lo = c1; hi = c2 - 1u; }
+                else hi = c1 - 1u;
             }
+            T = lo;
         }
     }
     uint32_t gt = 0u;
@@ -259,24 +265,24 @@ __device__ __forceinline__ void fill_new_rows(const Ctx &x, int Ncur) {
     const int *newlist = (const int *)(x.smem + Lt::NEW_OFF) + g * KT;
     const int nnew = ((const int *)(x.smem + Lt::MISC_OFF + 16))[g];
     constexpr int CH = H / 8;  // 16-byte chunks per row
-    for (int e = i; e < nnew * CH; e += H) {
-        const int q = e / CH, ch = e - q * CH;
+    constexpr int QS = H / CH;  // rows per pass of the group
+    const int ch = i % CH;
+    unsigned char *XA = x.smem + Lt::XA_OFF + (ch >> 3) * Lt::XA_SLICE;
+    const uint32_t c16 = (uint32_t)(ch & 7);
+    for (int q = i / CH; q < nnew; q += QS) {
         const int ent = newlist[q];
         const uint32_t row = (uint32_t)(g * KT + (ent & 0xffff));
         const int neuron = ent >> 16;
-        uint32_t val = 0u;
-        const int el = neuron & 7;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
         if ((neuron >> 3) == ch) {
             const float ga = score[Ncur + neuron];
             const __nv_bfloat16 b = SOUND ? __float2bfloat16_ru(ga) : __float2bfloat16_rn(ga);
             const uint32_t bits = (uint32_t)__bfloat16_as_ushort(b);
-            val = (el & 1) ? (bits << 16) : bits;
+            const int el = neuron & 7, wi = el >> 1;
+            const uint32_t w = (el & 1) ? (bits << 16) : bits;
+            val = make_uint4(wi == 0 ? w : 0u, wi == 1 ? w : 0u, wi == 2 ? w : 0u, wi == 3 ? w : 0u);
         }
-        const int wi = el >> 1;
-        unsigned char *XA = x.smem + Lt::XA_OFF + (ch >> 3) * Lt::XA_SLICE;
-        const uint32_t c16 = (uint32_t)(ch & 7);
-        *(uint4 *)(XA + row * 128u + ((c16 ^ (row & 7u)) << 4)) =
-            make_uint4(wi == 0 ? val : 0u, wi == 1 ? val : 0u, wi == 2 ? val : 0u, wi == 3 ? val : 0u);
+        *(uint4 *)(XA + row * 128u + ((c16 ^ (row & 7u)) << 4)) = val;
     }
 }
 
@@ -373,21 +379,36 @@ __device__ __forceinline__ float quad_scatter_ru(const float (&v)[4], int q) {
 // stores slot `2h + AB`. Column norms reduce-scatter across the lanes; kept
 // columns go to operand B by transposing stmatrix (row = position, 16 bytes
 // = eight consecutive neurons).
+//
+// Thread i's own neuron enters as its two center accumulators (TMEM columns
+// ccol, ccol + 1 of its lane), its bias and its |W_b| v sum xacc.
 template <int H, bool SOUND>
-__device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, int col0, float c_n, float xinf_n) {
+__device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, int col0, uint32_t ccol, float bias,
+                                float xacc) {
     using Lt = Layout<H>;
     const int g = x.g, lane = x.lane, wg = x.wg;
     float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
     const int quad = lane >> 2, qi = lane & 3;
-    float a[2][8][4];
+    float cc[2], a[2][8][4];
+    ptx::tmem_ld2(ccol, cc);
 #pragma unroll
     for (int h = 0; h < 2; ++h) ptx::tmem_ld16x256_x8(tl + ((uint32_t)(16 * h) << 16) + (uint32_t)col0, &a[h][0][0]);
+    ptx::tmem_wait_ld();
+    // center: D(c_hi) + D(c_lo) + bias, each add rounded once
+    const float c_n = (cc[0] + cc[1]) + bias;
+    float xinf_n;
+    if (SOUND) {
+        xinf_n = ru_mul(xacc, p.kappa);
+        // the two adds: u |cc0 + cc1| + u |c| <= 2^-23 (2 |c| + |bias|)
+        xinf_n = ru_fma(ru_add(2.f * fabsf(c_n), fabsf(bias)), 1.1920929e-07f, xinf_n);
+    } else {
+        xinf_n = xacc;
+    }
     // lane t%4 == q computes the scalars of slot q (neuron nq)
     const int nq = 32 * wg + 16 * (qi >> 1) + 8 * (qi & 1) + quad;
     const float cq = __shfl_sync(0xffffffffu, c_n, nq & 31);
     const float xq = __shfl_sync(0xffffffffu, xinf_n, nq & 31);
-    ptx::tmem_wait_ld();
     // range: noise magnitudes per neuron, reduce-scattered over the quad
     // (rounded up): lane q ends with slot q's sum
     float sa;
@@ -467,18 +488,23 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
         }
         xi = ru_add(xi, quad_scatter_ru(pd, qi));
     }
-    // kept old columns -> operand B rows g*KT + pos (dropped rows to a dummy area)
+    // kept old columns -> operand B rows g*KT + pos (dropped rows to a dummy
+    // area); pos counts the kept symbols below 8 j + r: whole bytes of the
+    // mask, then the low r bits of byte j
     {
         const int mi = lane >> 3, r = lane & 7;
         const int nb = 32 * wg + 8 * mi;
         const uint32_t xa = ptx::smem_u32(x.smem + Lt::XA_OFF + (nb >> 6) * Lt::XA_SLICE);
         const uint32_t c16 = (uint32_t)((nb & 63) >> 3);
         const uint32_t dummy = ptx::smem_u32(x.smem + Lt::DUMMY_OFF) + 16u * (uint32_t)lane;
+        const uint32_t below_r = (1u << r) - 1u;
+        uint32_t pre = 0u;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const int sym = 8 * j + r;
-            const bool k = (kept >> sym) & 1ull;
-            const uint32_t row = (uint32_t)(g * KT + __popcll(kept & ((1ull << sym) - 1ull)));
+            const uint32_t byte = (uint32_t)(kept >> (8 * j)) & 0xffu;
+            const bool k = (byte >> r) & 1u;
+            const uint32_t row = (uint32_t)(g * KT) + pre + (uint32_t)__popc(byte & below_r);
+            pre += (uint32_t)__popc(byte);
             const uint32_t addr = k ? xa + row * 128u + ((c16 ^ (row & 7u)) << 4) : dummy;
             uint32_t R[4];
 #pragma unroll
@@ -512,12 +538,17 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     x.abort_flag = (int *)(x.smem + Lt::MISC_OFF + 4);
     const int tid = x.tid, g = x.g, i = x.i;
     const int warp = tid >> 5;
+    // M tile m's MMAs are issued by lane 0 of warp m of group m (warps 0 and
+    // 9: two different schedulers); each issuer commits to the stage and
+    // accumulator barriers
+    constexpr int ISSUERS = Lt::MT;
+    const bool issuer = (i == 32 * g) && g < ISSUERS;
     if (tid == 0) {
         ptx::mbar_init(&x.bars[0], 1);
         ptx::mbar_init(&x.bars[1], 1);
-        ptx::mbar_init(&x.bars[2], 1 + NT / 32);
-        ptx::mbar_init(&x.bars[3], 1 + NT / 32);
-        ptx::mbar_init(&x.bars[4], 1);
+        ptx::mbar_init(&x.bars[2], ISSUERS + NT / 32);
+        ptx::mbar_init(&x.bars[3], ISSUERS + NT / 32);
+        ptx::mbar_init(&x.bars[4], ISSUERS);
         ptx::fence_mbar_init();
         *x.abort_flag = 0;
         uint32_t *sel = (uint32_t *)(x.smem + Lt::MISC_OFF + 32);
@@ -539,15 +570,19 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     const long long ntiles = (n + NB - 1) / NB;
     uint32_t gring = 0, accn = 0;
     // weight K slices stream through the ring in one global order (layer 1..L-2
-    // of every tile this CTA takes); thread 0 issues them up to two ahead of
-    // the consumers, across layer and tile boundaries, and never past the
-    // CTA's last slice
+    // of every tile this CTA takes); the producer thread issues them up to two
+    // ahead of the consumers, across layer and tile boundaries, and never past
+    // the CTA's last slice
     const int NL = p.L - 2;
     const long long my_tiles = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint32_t total_slices = (uint32_t)(my_tiles * NL * Lt::S);
+    // the copies are issued by lane 0 of the last warp, so that a refill,
+    // which waits for the MMAs that read the stage, never holds up the
+    // issue of the next slice's MMAs
+    constexpr int PRODUCER = NT - 32;
     uint32_t gload = 0;
     int ld_layer = 1, ld_slice = 0;
-    auto issue_upto = [&](uint32_t target) {  // thread 0
+    auto issue_upto = [&](uint32_t target) {  // the producer thread
         while (gload < target && gload < total_slices && !*x.abort_flag) {
             const uint32_t gg = gload, st = gg & 1u;
             if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, kSpin)) { fail(x, p, 3); return; }
@@ -617,22 +652,24 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             ptx::tc_fence_before();    // previous TMEM reads done before new MMAs
             __syncthreads();
             if (*x.abort_flag) break;
+            const float bias = p.b[l][i];  // read early: its latency hides under the MMA phase
             float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;  // rounded-up |W_b| v partials, boxes 0 and 1
             const uint32_t g0 = gring;
-            if (tid == 0) issue_upto(g0 + 2);  // no-op when prefetched during the last epilogue
+            if (tid == PRODUCER) issue_upto(g0 + 2);  // no-op when prefetched during the last epilogue
             const float *vg = (const float *)(x.smem + Lt::V_OFF) + g * H;
             for (int s = 0; s < Lt::S; ++s) {
                 const uint32_t gg = g0 + (uint32_t)s, st = gg & 1u, par = (gg >> 1) & 1u;
                 if (!ptx::mbar_wait(&x.bars[st], par, kSpin)) fail(x, p, 4);
                 unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
-                if (tid == 0 && !*x.abort_flag) {
+                if (issuer && !*x.abort_flag) {
                     ptx::tc_fence_after();
                     const uint32_t ia = ptx::idesc_bf16(128, NA + NCC);
                     for (int ks = 0; ks < 4; ++ks) {
                         const uint32_t acc = (s | ks) ? 1u : 0u;
                         const uint64_t bA =
                             ptx::desc_kmajor_sw128(ptx::smem_u32(x.smem + Lt::XA_OFF + s * Lt::XA_SLICE)) + 2 * ks;
-                        for (int m = 0; m < Lt::MT; ++m) {
+                        {
+                            const int m = g;
                             const uint64_t aB = ptx::desc_kmajor_sw128(ptx::smem_u32(base + m * Lt::TILE)) + 2 * ks;
                             const uint64_t aR =
                                 ptx::desc_kmajor_sw128(ptx::smem_u32(base + (Lt::MT + m) * Lt::TILE)) + 2 * ks;
@@ -645,7 +682,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 }
                 // x_inf' += |W_b| v from the resident slice: thread (g, i) takes
                 // row i over inputs 32 g .. 32 g + 31 of the slice for both boxes
-                // (one read and unpack of each weight, paired FMAs)
+                // (one read and unpack of each weight)
                 {
                     const int r = i & 127;
                     const unsigned char *row = base + m_of_thread * Lt::TILE + r * 128;
@@ -665,19 +702,21 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                             // |w| of the pair as floats (bf16 bits in the high half)
                             const float wlo = __uint_as_float((wq[e2] & 0x7fffu) << 16);
                             const float whi = __uint_as_float(wq[e2] & 0x7fff0000u);
-                            fma2_ru(xa0, xa1, wlo, whi, va[2 * e2], va[2 * e2 + 1]);
-                            fma2_ru(xb0, xb1, wlo, whi, vb[2 * e2], vb[2 * e2 + 1]);
+                            xa0 = ru_fma(wlo, va[2 * e2], xa0);
+                            xa1 = ru_fma(whi, va[2 * e2 + 1], xa1);
+                            xb0 = ru_fma(wlo, vb[2 * e2], xb0);
+                            xb1 = ru_fma(whi, vb[2 * e2 + 1], xb1);
                         }
                     }
                 }
                 __syncwarp();
                 if (x.lane == 0) ptx::mbar_arrive(&x.bars[2 + st]);
-                if (tid == 0) issue_upto(g0 + (uint32_t)s + 3);
+                if (tid == PRODUCER) issue_upto(g0 + (uint32_t)s + 3);
             }
             gring = g0 + Lt::S;
             if (!ptx::mbar_wait(&x.bars[4], accn & 1u, kSpin)) fail(x, p, 5);
             accn++;
-            if (tid == 0) issue_upto(gring + 2);  // next layer's (or tile's) first slices, during the epilogue
+            if (tid == PRODUCER) issue_upto(gring + 2);  // next layer's (or tile's) first slices, during the epilogue
             // the other group's box: hand over this thread's half of its |W_b| v
             float *xp = (float *)(x.smem + Lt::XP_OFF);
             const float xown = ru_add(g == 0 ? xa0 : xb0, g == 0 ? xa1 : xb1);
@@ -687,21 +726,8 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             if (*x.abort_flag) break;
             // ---- epilogue of the group's box -------------------------------
             const float xacc = ru_add(xown, xp[g * H + i]);
-            const float bias = p.b[l][i];
-            float cc[2];
-            ptx::tmem_ld2(tl + m_of_thread * TM_STRIDE + NA + 2 * g, cc);
-            ptx::tmem_wait_ld();
-            // center: D(c_hi) + D(c_lo) + bias, each add rounded once
-            const float c = (cc[0] + cc[1]) + bias;
-            float xinf;
-            if (SOUND) {
-                xinf = ru_mul(xacc, p.kappa);
-                // the two adds: u |cc0 + cc1| + u |c| <= 2^-23 (2 |c| + |bias|)
-                xinf = ru_fma(ru_add(2.f * fabsf(c), fabsf(bias)), 1.1920929e-07f, xinf);
-            } else {
-                xinf = xacc;
-            }
-            hidden_epilogue<H, SOUND>(x, p, tl, m_of_thread * TM_STRIDE + g * KT, c, xinf);
+            hidden_epilogue<H, SOUND>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
+                                      tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
         }
         __syncthreads();
         if (*x.abort_flag) break;
@@ -761,7 +787,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 }
             }
             group_sync(g, H);
-            if (i == 0 && bi < n) {
+            if (i == 32 * g && bi < n) {  // lane 0 of warp g of the group (warps 0 and H/32 + 1)
                 float rad = 0.f, esum = 0.f, y0 = 0.f, ey = 0.f, yinf = 0.f;
                 for (int k = 0; k < KT; ++k) {
                     float yk = 0.f, ek = 0.f;
