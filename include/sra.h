@@ -107,7 +107,10 @@ typedef struct {
     int32_t slope;       /* SRA_SLOPE_* */
     int32_t precision;   /* SRA_PREC_* */
     int32_t recheck;     /* 1: re-bound in FP64 every box whose lo or hi lies
-                            within the band of zero, and keep the FP64 result */
+                            within the band of zero, and keep the FP64 result;
+                            sra_cast_rays: march again in FP64 every ray with a
+                            step whose segment bound has an end, or whose point
+                            value lies, within the band of zero */
     float recheck_band;  /* band half-width relative to |center| + radius */
     int32_t split;       /* SRA_SPLIT_* */
     float delta;         /* convergence tolerance (Sec. 4.1), > 0 */
@@ -127,6 +130,9 @@ typedef struct {
                             delta / sqrt(3) whose six face centres take both signs is
                             returned as a leaf (counts[SRA_CNT_CONVERGED]); 0 = fixed
                             depth only */
+    int64_t *recheck_count; /* optional device int64 (NULL: not counted):
+                            sra_bound_boxes and sra_cast_rays add the number of
+                            boxes / rays their FP64 re-check took again */
 } sra_opts;
 
 /* Octree / k-d node: integer cell coordinates at `level` inside the root box
@@ -168,7 +174,8 @@ sra_status sra_free_mlp(sra_net *net);
  * lo[i], hi[i] (device float[n]) and the class cls[i] (device uint8[n]):
  * POSITIVE iff lo > 0, NEGATIVE iff hi < 0, else UNKNOWN. lo/hi may be NULL.
  * With opts->recheck the boxes whose lo or hi lies within the band of zero
- * are re-bounded in FP64 on the GPU and their lo/hi/cls replaced.
+ * are re-bounded in FP64 on the GPU and their lo/hi/cls replaced;
+ * opts->recheck_count, if given, counts them.
  * n == 0 is a no-op.
  * Errors: SRA_EINVAL, SRA_EUNSUPPORTED (K / width beyond the kernels' limits),
  * SRA_ECUDA. Asynchronous on `stream`. */
@@ -232,15 +239,22 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * t_hit[i] (device float[n]): the returned t on a hit, +inf for NO_HIT, NaN
  * when opts->max_iters ran out; and iters[i] (device int32[n], may be NULL):
  * loop iterations taken. One persistent launch refills finished ray slots.
- * opts->precision: SRA_PREC_FP32 runs every step on the SIMT cores in FP32
- * (any arithmetic); SRA_PREC_BF16 runs the hidden H -> H layers on the tensor
- * cores (tcgen05) with the weights and every operand split into BF16 hi/lo
- * pairs and FP32 accumulation (about 16 significant bits per product; plain
- * arithmetic, no rounding radius). BF16 needs affine-fixed arithmetic and a
- * network whose hidden layers all have one width H in {128, 256, 512}, with
- * 1 to 8 H -> H layers and an input width (after the encoding) of at most 64;
- * otherwise SRA_EUNSUPPORTED. A bounded wait of that kernel that runs out is
- * reported by sra_sync_status as SRA_ETIMEOUT.
+ * opts->precision: SRA_PREC_FP32 (and SRA_PREC_FP64) runs every step on the
+ * SIMT cores in FP32 (FP64), any arithmetic; SRA_PREC_BF16 runs the hidden
+ * H -> H layers on the tensor cores (tcgen05) with the weights and every
+ * operand split into BF16 hi/lo pairs and FP32 accumulation (about 16
+ * significant bits per product; plain arithmetic, no rounding radius). BF16
+ * needs affine-fixed arithmetic and a network whose hidden layers all have
+ * one width H in {128, 256, 512}, with 1 to 8 H -> H layers and an input
+ * width (after the encoding) of at most 64; otherwise SRA_EUNSUPPORTED. A
+ * bounded wait of that kernel that runs out is reported by sra_sync_status as
+ * SRA_ETIMEOUT. With opts->recheck (FP32 or BF16) a ray that took a step
+ * whose segment bound [y0 - rad, y0 + rad] has an end within
+ * recheck_band (|y0| + rad) of zero, or whose point value fc lies within
+ * recheck_band (|y0| + rad + |fc|) of zero, is marched again from its start
+ * in FP64 (its origin's sign too) and its t_hit and iters are the FP64 ones;
+ * opts->recheck_count, if given, counts those rays. n is at most 2^31 - 1.
+ * Uses stream-ordered scratch of 4 bytes per ray (8 with recheck).
  * Errors: SRA_EINVAL (delta <= 0, bad steps), SRA_EUNSUPPORTED, SRA_ECUDA.
  * Asynchronous. */
 sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *origins,

@@ -111,7 +111,7 @@ sra_status make_cfg(const sra_net *n, const sra_opts *o, int kmax, int tsize, in
     cfg->src_off = (int)off;
     off = align16(off + (size_t)kmax * 2);
     cfg->ray_off = (int)off;
-    off = align16(off + sizeof(RaySlotState));
+    off = align16(off + (tsize == 8 ? sizeof(RaySlotState<double>) : sizeof(RaySlotState<float>)));
     cfg->slot_bytes = (int)off;
     const int maxT = engine_max_threads(tsize, kmax);
     if (n->H > maxT)
@@ -666,7 +666,7 @@ sra_status sra_bound_boxes(const sra_net *n, const sra_opts *o, const float *cen
     out.lo = lo;
     out.hi = hi;
     out.cls = cls;
-    return bound_with_recheck(n, o, src, out, count, nullptr, as_stream(stream));
+    return bound_with_recheck(n, o, src, out, count, (unsigned long long *)o->recheck_count, as_stream(stream));
 }
 
 sra_status sra_eval(const sra_net *n, const float *x, int64_t count, float *y, void *stream) {
@@ -1056,6 +1056,53 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     return SRA_OK;
 }
 
+// The plain forward pass f(x) at count points (zero-width intervals), in
+// FP32 or FP64; with a list only at the listed points (y indexed by point).
+static sra_status eval_points(const sra_net *n, bool fp64, const float *x, int64_t count, float *y,
+                              const int *list, const int *list_count, cudaStream_t st) {
+    sra_opts o;
+    sra_default_opts(&o);
+    o.arith = SRA_ARITH_INTERVAL;
+    BoxSrc src;
+    memset(&src, 0, sizeof src);
+    src.kind = SRC_POINTS;
+    src.centers = x;
+    src.n = count;
+    src.list = list;
+    src.list_count = list_count;
+    BoundOut out;
+    memset(&out, 0, sizeof out);
+    out.lo = y;
+    return run_bound(n, &o, fp64, 1, src, out, count, st);
+}
+
+// The persistent SIMT ray kernel (FP32 or FP64) over rp (every field but the
+// march options, which come from o); n_hint bounds the rays it can take.
+static sra_status launch_rays(const sra_net *n, const sra_opts *o, bool fp64, RayParams rp, int64_t n_hint,
+                              cudaStream_t st) {
+    int kmax = 0;
+    sra_status r = kmax_for(n, o, 1, &kmax);
+    if (r) return r;
+    RangeCfg cfg;
+    if ((r = make_cfg(n, o, kmax, fp64 ? 8 : 4, 512, &cfg))) return r;
+    rp.delta = o->delta;
+    rp.t_max = o->t_max;
+    rp.sigma0 = o->sigma0;
+    rp.eta_plus = o->eta_plus;
+    rp.eta_minus = o->eta_minus;
+    rp.safety = o->safety;
+    rp.max_iters = o->max_iters;
+    const int per_sm = fp64 ? rays_blocks_per_sm_f64(kmax, cfg) : rays_blocks_per_sm_f32(kmax, cfg);
+    long long grid = (long long)per_sm * num_sms();
+    const long long need = (n_hint + cfg.NB - 1) / cfg.NB;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    cudaError_t e = fp64 ? launch_rays_f64(kmax, n->dev, &rp, cfg, (int)grid, st)
+                         : launch_rays_f32(kmax, n->dev, &rp, cfg, (int)grid, st);
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "ray kernel launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
 // Proc. 2 for `count` rays, resuming each ray from (t_start[i], sigma_start[i])
 // when those are given (the hand-over of frustum casting).
 static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const float *origins, const float *dirs,
@@ -1072,22 +1119,39 @@ static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const floa
         o->max_iters < 1)
         return fail(SRA_EINVAL, "ray options out of range (delta, t_max, sigma0 > 0; eta+ >= 1; "
                                 "0 < eta- < 1; 0 < safety <= 1; max_iters >= 1)");
-    const bool tc = o->precision == SRA_PREC_BF16;
-    if (o->precision != SRA_PREC_FP32 && !tc)
-        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32 or (tensor cores) BF16");
+    const bool tc = o->precision == SRA_PREC_BF16, fp64 = o->precision == SRA_PREC_FP64;
+    if (o->precision != SRA_PREC_FP32 && !tc && !fp64)
+        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32, FP64 or (tensor cores) BF16");
     if (tc && (!n->tcr_ok || o->arith != SRA_ARITH_AFFINE_FIXED))
         return fail(SRA_EUNSUPPORTED, "BF16 cast_rays needs affine-fixed arithmetic and a net of "
                                       "uniform hidden width 128/256/512 with 1..%d hidden layers and "
                                       "input width <= %d", kMaxRayTc, tc_ray_max_din());
+    if (count > INT32_MAX) return fail(SRA_EINVAL, "n > 2^31 - 1");
+    const bool recheck = o->recheck && !fp64;
     cudaStream_t st = as_stream(stream);
+    float *f0;
+    int *flags = nullptr, *cnt;
+    unsigned long long *next;
+    auto carve = [&](Carve &c) {
+        f0 = c.take<float>(count);
+        if (recheck) flags = c.take<int>(count);
+        next = c.take<unsigned long long>(2);  // [0] main march, [1] FP64 re-check
+        cnt = c.take<int>(4);                  // [0] flagged rays
+    };
+    Carve sizing;
+    carve(sizing);
     Scratch sc;
-    const size_t f0_bytes = align16((size_t)count * 4);
-    if ((r = scratch_alloc(sc, f0_bytes + 16, st))) return r;
-    float *f0 = (float *)sc.p;
-    unsigned long long *next = (unsigned long long *)((char *)sc.p + f0_bytes);
-    // f(p) at every origin: the reference sign of DifferentSigns (Proc. 2)
-    if ((r = sra_eval(n, origins, count, f0, stream))) return r;
-    SRA_CK(cudaMemsetAsync(next, 0, 8, st));
+    if ((r = scratch_alloc(sc, sizing.off, st))) return r;
+    Carve cv;
+    cv.base = (char *)sc.p;
+    cv.cap = sizing.off;
+    carve(cv);
+    if (cv.overflow) return fail(SRA_ECUDA, "ray scratch layout exceeds its allocation");
+    SRA_CK(cudaMemsetAsync(next, 0, 2 * sizeof(unsigned long long), st));
+    SRA_CK(cudaMemsetAsync(cnt, 0, 4 * sizeof(int), st));
+    // f(p) at every origin, in the march's precision: the reference sign of
+    // DifferentSigns (Proc. 2)
+    if ((r = eval_points(n, fp64, origins, count, f0, nullptr, nullptr, st))) return r;
     if (tc) {
         TcRayParams p = n->tcrp;
         p.slope = o->slope;
@@ -1107,17 +1171,35 @@ static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const floa
         p.eta_minus = o->eta_minus;
         p.safety = o->safety;
         p.max_iters = o->max_iters;
+        p.flag_list = flags;
+        p.flag_count = cnt;
+        p.band = o->recheck_band;
         long long grid = num_sms();
         const long long need = (count + tc_ray_slots() - 1) / tc_ray_slots();
         if (grid > need) grid = need;
         cudaError_t e = launch_tc_rays(n->tcr_H, p, (int)grid, st);
         if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core ray kernel launch: %s", cudaGetErrorString(e));
-        return SRA_OK;
+    } else {
+        RayParams rp;
+        memset(&rp, 0, sizeof rp);
+        rp.origins = origins;
+        rp.dirs = dirs;
+        rp.f0 = f0;
+        rp.t_hit = t_hit;
+        rp.iters = iters;
+        rp.t_start = t_start;
+        rp.sigma_start = sigma_start;
+        rp.n = count;
+        rp.next = next;
+        rp.flag_list = flags;
+        rp.flag_count = cnt;
+        rp.band = o->recheck_band;
+        if ((r = launch_rays(n, o, fp64, rp, count, st))) return r;
     }
-    int kmax = 0;
-    if ((r = kmax_for(n, o, 1, &kmax))) return r;
-    RangeCfg cfg;
-    if ((r = make_cfg(n, o, kmax, 4, 512, &cfg))) return r;
+    if (!recheck) return SRA_OK;
+    // FP64 re-check: the flagged rays march again from their start in FP64
+    // (their origin signs too) and overwrite their results
+    if ((r = eval_points(n, true, origins, count, f0, flags, cnt, st))) return r;
     RayParams rp;
     memset(&rp, 0, sizeof rp);
     rp.origins = origins;
@@ -1128,21 +1210,11 @@ static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const floa
     rp.t_start = t_start;
     rp.sigma_start = sigma_start;
     rp.n = count;
-    rp.next = next;
-    rp.delta = o->delta;
-    rp.t_max = o->t_max;
-    rp.sigma0 = o->sigma0;
-    rp.eta_plus = o->eta_plus;
-    rp.eta_minus = o->eta_minus;
-    rp.safety = o->safety;
-    rp.max_iters = o->max_iters;
-    const int per_sm = rays_blocks_per_sm_f32(kmax, cfg);
-    long long grid = (long long)per_sm * num_sms();
-    const long long need = (count + cfg.NB - 1) / cfg.NB;
-    if (grid > need) grid = need;
-    cudaError_t e = launch_rays_f32(kmax, n->dev, &rp, cfg, (int)grid, st);
-    if (e != cudaSuccess) return fail(SRA_ECUDA, "ray kernel launch: %s", cudaGetErrorString(e));
-    return SRA_OK;
+    rp.next = next + 1;
+    rp.list = flags;
+    rp.list_count = cnt;
+    rp.recheck_counter = (unsigned long long *)o->recheck_count;
+    return launch_rays(n, o, true, rp, count, st);
 }
 
 sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *eye, const float *dirs, int32_t W,

@@ -510,25 +510,31 @@ multi_bound_kernel(const BatchSegDev *segs, const int *order, int nseg, long lon
 // Ray kernel: CastRay (Proc. 2), persistent over ray slots. Each iteration a
 // slot bounds the segment [t, t+sigma] (c = p + (t + sigma/2) r,
 // v = (sigma/2) r) and evaluates f(p + (t + delta) r) in the same pass.
+// With rp.list the slots take the listed rays only (the FP64 re-check);
+// with rp.flag_list a ray that met a near-zero decision is listed when it ends.
 template <typename T, int KMAX>
 __global__ void __launch_bounds__(MaxThreads<T, KMAX>::value)
 ray_kernel(NetDev net, RayParams rp, RangeCfg cfg) {
     extern __shared__ __align__(16) char smem[];
     const int slot = threadIdx.x / cfg.H, i = threadIdx.x - slot * cfg.H;
     const Slot<T> s = carve<T>(smem, slot, cfg);
-    RaySlotState *st = (RaySlotState *)s.ray;
+    RaySlotState<T> *st = (RaySlotState<T> *)s.ray;
     if (i == 0) st->idx = -1;
     __syncthreads();
     for (;;) {
         if (i == 0 && st->idx < 0) {
-            const unsigned long long q = atomicAdd(rp.next, 1ull);
-            if ((long long)q < rp.n) {
-                st->idx = (long long)q;
-                st->t = rp.t_start ? rp.t_start[q] : 0.f;
-                st->sigma = rp.sigma_start ? rp.sigma_start[q] : rp.sigma0;
+            const unsigned long long k = atomicAdd(rp.next, 1ull);
+            const long long n_rays = rp.list ? (long long)*rp.list_count : rp.n;
+            if ((long long)k < n_rays) {
+                const long long q = rp.list ? (long long)rp.list[k] : (long long)k;
+                st->idx = q;
+                st->t = rp.t_start ? T(rp.t_start[q]) : T(0);
+                st->sigma = rp.sigma_start ? T(rp.sigma_start[q]) : T(rp.sigma0);
                 st->iters = 0;
                 st->f0pos = rp.f0[q] >= 0.f;
                 st->live = 1;
+                st->flag = 0;
+                if (rp.recheck_counter) atomicAdd(rp.recheck_counter, 1ull);
             } else {
                 st->live = 0;
             }
@@ -567,6 +573,7 @@ ray_kernel(NetDev net, RayParams rp, RangeCfg cfg) {
             const T y0 = s.outv[0], rad = s.outv[1], fc = s.outv[2];
             const long long q = st->idx;
             st->iters += 1;
+            if (rp.flag_list && near_zero_step<T>(y0, rad, fc, rp.band)) st->flag = 1;
             bool done = false;
             float result = 0.f;
             if ((fc >= T(0)) != (st->f0pos != 0)) {  // DifferentSigns at t + delta
@@ -574,16 +581,17 @@ ray_kernel(NetDev net, RayParams rp, RangeCfg cfg) {
                 result = st->t;
             } else {
                 const int k = classify_range(y0 - rad, y0 + rad);
-                float sstar;
-                if (k != SRA_UNKNOWN) { sstar = st->sigma; st->sigma *= rp.eta_plus; }
-                else { sstar = 0.f; st->sigma *= rp.eta_minus; }
-                st->t += fmaxf(rp.safety * sstar, rp.delta);
-                if (!(st->t < rp.t_max)) { done = true; result = INFINITY; }
+                T sstar;
+                if (k != SRA_UNKNOWN) { sstar = st->sigma; st->sigma *= T(rp.eta_plus); }
+                else { sstar = T(0); st->sigma *= T(rp.eta_minus); }
+                st->t += fmax(T(rp.safety) * sstar, T(rp.delta));
+                if (!(st->t < T(rp.t_max))) { done = true; result = INFINITY; }
             }
             if (!done && st->iters >= rp.max_iters) { done = true; result = NAN; }
             if (done) {
                 rp.t_hit[q] = result;
                 if (rp.iters) rp.iters[q] = st->iters;
+                if (rp.flag_list && st->flag) rp.flag_list[atomicAdd(rp.flag_count, 1)] = (int)q;
                 st->idx = -1;
             }
         }

@@ -37,6 +37,9 @@ struct RayParams;
 cudaError_t launch_rays_f32(int kmax, const NetDev &net, const void *rp, const RangeCfg &cfg,
                             int grid, cudaStream_t st);
 int rays_blocks_per_sm_f32(int kmax, const RangeCfg &cfg);
+cudaError_t launch_rays_f64(int kmax, const NetDev &net, const void *rp, const RangeCfg &cfg,
+                            int grid, cudaStream_t st);
+int rays_blocks_per_sm_f64(int kmax, const RangeCfg &cfg);
 
 // Frontier round (Proc. 3 split) after classification.
 struct SplitArgs {

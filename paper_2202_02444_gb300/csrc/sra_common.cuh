@@ -97,7 +97,8 @@ struct BatchSegDev {
     long long chunk0;  // first chunk (group of NB nodes) of the segment in its launch
 };
 
-// CastRay (Proc. 2) launch parameters and per-slot state.
+// CastRay (Proc. 2) launch parameters and per-slot state. Every per-ray
+// array is indexed by the ray's own index.
 struct RayParams {
     const float *origins, *dirs, *f0;
     const float *t_start, *sigma_start;  // optional per-ray march state to resume from
@@ -107,15 +108,36 @@ struct RayParams {
     unsigned long long *next;  // global ray counter
     float delta, t_max, sigma0, eta_plus, eta_minus, safety;
     long long max_iters;
+    // optional: march only the rays list[0 .. *list_count) (their indices),
+    // adding one to *recheck_counter (if given) per ray taken
+    const int *list, *list_count;
+    unsigned long long *recheck_counter;
+    // optional: append each ray that met a decision near zero (near_zero_step)
+    // once, when it ends, to flag_list[atomicAdd(flag_count, 1)]
+    int *flag_list, *flag_count;
+    float band;
 };
 
-struct RaySlotState {
+// The march state (t, sigma) is kept in the kernel's precision.
+template <typename T> struct RaySlotState {
     long long idx;  // ray index, -1 idle
-    float t, sigma;
+    T t, sigma;
     int f0pos;
     int iters;
     int live;
+    int flag;  // a decision of this ray was near zero
 };
+
+// A march step whose decision the FP64 re-check takes again: the segment
+// bound [y0 - rad, y0 + rad] has an end within band (|y0| + rad) of zero, or
+// the point value fc (the DifferentSigns test) lies within band (|y0| + rad +
+// |fc|) of zero. Both are the cases where the rounding of a lower precision
+// can flip a class or a sign.
+template <typename T>
+__device__ __forceinline__ bool near_zero_step(T y0, T rad, T fc, float band) {
+    const T scale = fabs(y0) + rad, b = (T)band;
+    return fabs(y0 - rad) <= b * scale || fabs(y0 + rad) <= b * scale || fabs(fc) <= b * (scale + fabs(fc));
+}
 
 template <typename T> struct Num;
 template <> struct Num<float> {

@@ -48,7 +48,7 @@ enum { X_HI = 0, X_LO = 16 };
 struct RaySlot {
     long long idx;
     float t, sigma;
-    int f0pos, iters, live, pad;
+    int f0pos, iters, live, flag;  // flag: a decision of this ray was near zero
 };
 
 constexpr int align1k(int x) { return (x + 1023) & ~1023; }
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                     s.iters = 0;
                     s.f0pos = p.f0[q] >= 0.f;
                     s.live = 1;
+                    s.flag = 0;
                 } else {
                     s.live = 0;
                     s.idx = 0x7fffffffffffffffll;  // the ray list is exhausted for this slot
@@ -393,6 +394,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             }
             const float y0 = sums[0] + p.bout, rad = fabsf(sums[1]) + sums[2], fc = sums[3] + p.bout;
             s.iters += 1;
+            if (p.flag_list && near_zero_step<float>(y0, rad, fc, p.band)) s.flag = 1;
             bool done = false;
             float result = 0.f;
             if ((fc >= 0.f) != (s.f0pos != 0)) {  // DifferentSigns at t + delta
@@ -410,6 +412,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             if (done) {
                 p.t_hit[s.idx] = result;
                 if (p.iters) p.iters[s.idx] = s.iters;
+                if (p.flag_list && s.flag) p.flag_list[atomicAdd(p.flag_count, 1)] = (int)s.idx;
                 s.idx = -1;
             }
         }

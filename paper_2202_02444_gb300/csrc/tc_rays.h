@@ -35,6 +35,10 @@ struct TcRayParams {
     unsigned long long *next;
     float delta, t_max, sigma0, eta_plus, eta_minus, safety;
     long long max_iters;
+    // optional: each ray that met a near-zero decision (near_zero_step) is
+    // appended once, when it ends, to flag_list[atomicAdd(flag_count, 1)]
+    int *flag_list, *flag_count;
+    float band;
 };
 
 int tc_ray_smem_bytes(int H);

@@ -50,7 +50,8 @@ class Opts(C.Structure):
                 ("split", C.c_int32), ("delta", C.c_float), ("t_max", C.c_float),
                 ("sigma0", C.c_float), ("eta_plus", C.c_float), ("eta_minus", C.c_float),
                 ("safety", C.c_float), ("max_iters", C.c_int64),
-                ("block_threads", C.c_int32), ("converge", C.c_int32)]
+                ("block_threads", C.c_int32), ("converge", C.c_int32),
+                ("recheck_count", C.c_void_p)]
 
 
 class Request(C.Structure):
@@ -121,7 +122,9 @@ def _check(code):
 def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=False,
               recheck_band=1e-5, split="octree", delta=None, t_max=None, sigma0=None,
               eta_plus=None, eta_minus=None, safety=None, max_iters=None, block_threads=0,
-              converge=False):
+              converge=False, recheck_count=None):
+    """sra_opts; recheck_count is an optional CUDA int64 tensor that the FP64
+    re-check adds its box / ray count to (the caller keeps it alive)."""
     o = Opts()
     _lib.sra_default_opts(C.byref(o))
     o.arith = ARITH[arith] if isinstance(arith, str) else int(arith)
@@ -141,7 +144,16 @@ def make_opts(arith="fixed", K=0, slope="chebyshev", precision="fp32", recheck=F
         o.max_iters = int(max_iters)
     o.block_threads = int(block_threads)
     o.converge = int(bool(converge))
+    if recheck_count is not None:
+        _need_count(recheck_count)
+        o.recheck_count = recheck_count.data_ptr()
     return o
+
+
+def _need_count(t):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and t.numel() >= 1
+            and t.is_contiguous()):
+        raise ValueError("recheck_count must be a contiguous CUDA int64 tensor")
 
 
 def _stream():
