@@ -56,7 +56,7 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true>": {"sha1": "22cf6170d6d53740c5b60adc943d9e75cb754399", "bytes": 3289600,
+    "tc_bound_kernel<256,true>": {"sha1": "bd75a260610dad4002be7345877fbe2f4d556025", "bytes": 3051520,
                                   "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
@@ -580,14 +580,19 @@ def main():
         d2h_list.append(cnt_host.numel() * 8 + nch * 8)
 
     # ray phase (separate from the step): a camera tile with an iteration cap,
-    # in each form: FP32 on the SIMT cores, split-BF16 hidden layers on tcgen05
+    # in each form: FP32 on the SIMT cores, split-BF16 hidden layers on tcgen05,
+    # and the latter with the FP64 re-check of rays that met a near-zero decision
     ray_forms, ray_t = {}, {}
     it_flop = ray_iter_flops(mlp_ray)
-    for prec in ("fp32", "bf16"):
+    rechecked = torch.zeros(1, dtype=torch.int64, device=dev)
+    for form in ("fp32", "bf16", "bf16_fp64_recheck"):
+        prec = "bf16" if form.startswith("bf16") else form
         ropts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_iters,
-                              precision=prec)
+                              precision=prec, recheck=form.endswith("recheck"), recheck_band=1e-5,
+                              recheck_count=rechecked)
         sra.cast_rays(net_ray, ro[:64], rd[:64], opts=ropts)
         torch.cuda.synchronize()
+        rechecked.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         sra.cast_rays(net_ray, ro, rd, opts=ropts, t_hit=t_hit, iters=iters)
@@ -598,14 +603,17 @@ def main():
         iters_h = iters.cpu().numpy()
         t_h = t_hit.cpu().numpy()
         done = ~np.isnan(t_h)
-        ray_t[prec] = t_h
-        ray_forms[prec] = {
+        ray_t[form] = t_h
+        ray_forms[form] = {
             "ms": ray_ms, "rays": R, "completed": int(done.sum()),
             "rays_per_s": float(done.sum()) / (ray_ms / 1e3),
             "ray_iters_per_s": float(iters_h.sum()) / (ray_ms / 1e3),
             "tflops": float(iters_h.sum()) * it_flop / (ray_ms / 1e3) / 1e12,
             "iters_mean": float(iters_h.mean()), "iters_max": int(iters_h.max()),
             "hits": int(np.isfinite(t_h).sum())}
+        if form.endswith("recheck"):
+            ray_forms[form]["rays_rechecked_fp64"] = int(rechecked.item())
+            ray_forms[form]["recheck_band"] = 1e-5
     ta, tb = ray_t["fp32"], ray_t["bf16"]
     fin = np.isfinite(ta) & np.isfinite(tb)
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))

@@ -109,8 +109,8 @@ typedef struct {
     int32_t recheck;     /* 1: re-bound in FP64 every box whose lo or hi lies
                             within the band of zero, and keep the FP64 result;
                             sra_cast_rays: march again in FP64 every ray with a
-                            step whose segment bound has an end, or whose point
-                            value lies, within the band of zero */
+                            step whose segment bound has an end within the
+                            band of zero */
     float recheck_band;  /* band half-width relative to |center| + radius */
     int32_t split;       /* SRA_SPLIT_* */
     float delta;         /* convergence tolerance (Sec. 4.1), > 0 */
@@ -250,9 +250,8 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * bounded wait of that kernel that runs out is reported by sra_sync_status as
  * SRA_ETIMEOUT. With opts->recheck (FP32 or BF16) a ray that took a step
  * whose segment bound [y0 - rad, y0 + rad] has an end within
- * recheck_band (|y0| + rad) of zero, or whose point value fc lies within
- * recheck_band (|y0| + rad + |fc|) of zero, is marched again from its start
- * in FP64 (its origin's sign too) and its t_hit and iters are the FP64 ones;
+ * recheck_band (|y0| + rad) of zero is marched again from its start in FP64
+ * (its origin's sign too) and its t_hit and iters are the FP64 ones;
  * opts->recheck_count, if given, counts those rays. n is at most 2^31 - 1.
  * Uses stream-ordered scratch of 4 bytes per ray (8 with recheck).
  * Errors: SRA_EINVAL (delta <= 0, bad steps), SRA_EUNSUPPORTED, SRA_ECUDA.

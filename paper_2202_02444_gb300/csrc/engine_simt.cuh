@@ -573,7 +573,7 @@ ray_kernel(NetDev net, RayParams rp, RangeCfg cfg) {
             const T y0 = s.outv[0], rad = s.outv[1], fc = s.outv[2];
             const long long q = st->idx;
             st->iters += 1;
-            if (rp.flag_list && near_zero_step<T>(y0, rad, fc, rp.band)) st->flag = 1;
+            if (rp.flag_list && near_zero_step<T>(y0, rad, rp.band)) st->flag = 1;
             bool done = false;
             float result = 0.f;
             if ((fc >= T(0)) != (st->f0pos != 0)) {  // DifferentSigns at t + delta

@@ -129,14 +129,15 @@ template <typename T> struct RaySlotState {
 };
 
 // A march step whose decision the FP64 re-check takes again: the segment
-// bound [y0 - rad, y0 + rad] has an end within band (|y0| + rad) of zero, or
-// the point value fc (the DifferentSigns test) lies within band (|y0| + rad +
-// |fc|) of zero. Both are the cases where the rounding of a lower precision
-// can flip a class or a sign.
+// bound [y0 - rad, y0 + rad] has an end within band (|y0| + rad) of zero, the
+// case where the rounding of a lower precision can flip the segment's class
+// (the rule of the box re-check). A wrong sign of the point value fc near
+// zero needs no re-check: a root then lies within about delta of the point,
+// which the delta semantics of Proc. 2 accept.
 template <typename T>
-__device__ __forceinline__ bool near_zero_step(T y0, T rad, T fc, float band) {
+__device__ __forceinline__ bool near_zero_step(T y0, T rad, float band) {
     const T scale = fabs(y0) + rad, b = (T)band;
-    return fabs(y0 - rad) <= b * scale || fabs(y0 + rad) <= b * scale || fabs(fc) <= b * (scale + fabs(fc));
+    return fabs(y0 - rad) <= b * scale || fabs(y0 + rad) <= b * scale;
 }
 
 template <typename T> struct Num;

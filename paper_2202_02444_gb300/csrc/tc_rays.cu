@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             }
             const float y0 = sums[0] + p.bout, rad = fabsf(sums[1]) + sums[2], fc = sums[3] + p.bout;
             s.iters += 1;
-            if (p.flag_list && near_zero_step<float>(y0, rad, fc, p.band)) s.flag = 1;
+            if (p.flag_list && near_zero_step<float>(y0, rad, p.band)) s.flag = 1;
             bool done = false;
             float result = 0.f;
             if ((fc >= 0.f) != (s.f0pos != 0)) {  // DifferentSigns at t + delta
