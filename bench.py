@@ -99,6 +99,8 @@ def parse_args():
     ap.add_argument("--frontier-level", type=int, default=7)
     ap.add_argument("--ray-tile", type=int, default=64, help="ray tile side (tile^2 rays)")
     ap.add_argument("--ray-iters", type=int, default=500, help="per-ray iteration cap of the ray phase")
+    ap.add_argument("--ray-complete-cap", type=int, default=40000,
+                    help="iteration cap of the ray completion sample (0: skip it)")
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None,
@@ -614,6 +616,31 @@ def main():
         if form.endswith("recheck"):
             ray_forms[form]["rays_rechecked_fp64"] = int(rechecked.item())
             ray_forms[form]["recheck_band"] = 1e-5
+    # completion sample: one full wave of the tensor-core kernel (16 ray slots
+    # per SM) of central-tile rays marched to the end; rays/s of each form is
+    # its measured iteration rate over the sample's mean iterations per ray
+    completion = None
+    if args.ray_complete_cap > 0:
+        nc = min(R, 16 * torch.cuda.get_device_properties(dev).multi_processor_count)
+        copts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_complete_cap,
+                              precision="bf16")
+        tc_, ic_ = t_hit[:nc], iters[:nc]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sra.cast_rays(net_ray, ro[:nc], rd[:nc], opts=copts, t_hit=tc_, iters=ic_)
+        e1.record()
+        torch.cuda.synchronize()
+        sra.sync_status(net_ray)
+        c_ms = e0.elapsed_time(e1)
+        t_c, i_c = tc_.cpu().numpy(), ic_.cpu().numpy()
+        ended = ~np.isnan(t_c)
+        it_mean = float(i_c[ended].mean()) if ended.any() else float("nan")
+        completion = {"rays": int(nc), "form": "bf16", "cap": args.ray_complete_cap, "ms": c_ms,
+                      "completed": int(ended.sum()), "hits": int(np.isfinite(t_c).sum()),
+                      "rays_per_s": float(ended.sum()) / (c_ms / 1e3),
+                      "iters_per_completed_ray": it_mean}
+        for form, rf in ray_forms.items():
+            rf["rays_per_s_at_sample_iters"] = rf["ray_iters_per_s"] / it_mean if ended.any() else None
     ta, tb = ray_t["fp32"], ray_t["bf16"]
     fin = np.isfinite(ta) & np.isfinite(tb)
     agree = (np.isfinite(ta) == np.isfinite(tb)) & (np.isnan(ta) == np.isnan(tb))
@@ -766,7 +793,7 @@ def main():
             "rays": {"workload": f"{T}x{T} central pixels of a 1920x1080 camera at (0,0,3) vs ELU "
                                  f"39(PE 6 octaves)-[512]x6-1, affine-fixed, delta 1e-4, t_max 10, "
                                  f"cap {args.ray_iters} iterations per ray",
-                     "flop_per_iter": it_flop, "forms": ray_forms,
+                     "flop_per_iter": it_flop, "forms": ray_forms, "completion_sample": completion,
                      "same_outcome_frac": float(agree.mean()),
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
                      / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
