@@ -92,7 +92,7 @@ def measured_peak(key, fallback):
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--batch", type=int, default=1 << 17, help="octree nodes per step")
@@ -139,7 +139,7 @@ class ClockSampler:
             try:
                 self.proc = subprocess.Popen(
                     ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                     "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                     "-lms", "25"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             except OSError:
                 self.proc = None
         return self

@@ -682,15 +682,21 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 }
                 // x_inf' += |W_b| v from the resident slice: thread (g, i) takes
                 // row i over inputs 32 g .. 32 g + 31 of the slice for both boxes
-                // (one read and unpack of each weight)
+                // (one read and unpack of each weight), in four 8-input chunks
                 {
                     const int r = i & 127;
                     const unsigned char *row = base + m_of_thread * Lt::TILE + r * 128;
                     const float *v0 = (const float *)(x.smem + Lt::V_OFF) + s * 64;
                     const float *v1 = v0 + H;
+                    // the MMA-issuing warps leave their last chunk to the other
+                    // group's warp over the same rows, which sums it into the
+                    // same row's partials (every partial rounded up)
+                    const bool light = x.wg == g && g < ISSUERS;
+                    const bool heavy = x.wg == 1 - g && 1 - g < ISSUERS;
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        const int ch = 4 * g + cc;
+                    for (int cc = 0; cc < 5; ++cc) {
+                        if ((cc == 3 && light) || (cc == 4 && !heavy)) continue;
+                        const int ch = cc < 4 ? 4 * g + cc : 4 * (1 - g) + 3;
                         const uint4 q = *(const uint4 *)(row + (((ch ^ (r & 7)) & 7) << 4));
                         const float4 a0 = *(const float4 *)(v0 + ch * 8), a1 = *(const float4 *)(v0 + ch * 8 + 4);
                         const float4 b0 = *(const float4 *)(v1 + ch * 8), b1 = *(const float4 *)(v1 + ch * 8 + 4);
