@@ -18,7 +18,8 @@
 // The weights stream from L2 by TMA as 16 KB tiles (128 rows x 64 K of one
 // matrix) through a ring that runs ahead across layers and march steps. One
 // thread issues the copies (it refills a stage once the MMAs that read it
-// have completed), another issues the MMAs (one tile = 4 MMAs of K = 16),
+// have completed), another issues the MMAs (one tile = 4 MMAs of K = 16;
+// tiles in pairs, a D tile and a Dx tile, their MMAs alternating),
 // and the whole CTA then runs the epilogue: per neuron and ray, the range,
 // the activation rule (App. A) and the operand rows of the next layer. The
 // encoding, the output layer and the march state run on the SIMT cores in
@@ -118,7 +119,11 @@ __device__ __forceinline__ void activate(int act, int slope, float &c, float &A,
 
 // A ring unit: one 128 x 64 tile (M tile m, K slice s) of one of the four
 // matrices of linear layer `layer`. Within a layer the units run K slice by
-// K slice, M tile by M tile, matrix by matrix (W_b, W_r, |W_b|, sign W_r).
+// K slice, M tile by M tile, matrix by matrix in the order W_b, |W_b|, W_r,
+// sign W_r, so that consecutive units feed the two accumulators D and Dx: the
+// MMA thread takes them in pairs and alternates their MMAs, and neither
+// chain of dependent accumulations waits on itself back to back. Each
+// accumulator still receives W_b's products before W_r's.
 struct Unit {
     int layer, s, m, which;
 };
@@ -127,7 +132,7 @@ template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
     using L = RL<H>;
     Unit r;
     r.layer = layer;
-    r.which = u & 3;
+    r.which = (u & 1) * 2 + ((u >> 1) & 1);  // 0 W_b, 2 |W_b|, 1 W_r, 3 sign W_r
     const int ms = u >> 2;
     r.m = ms & (L::MT - 1);
     r.s = ms / L::MT;
@@ -306,25 +311,40 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             } else if (issuer) {
                 bool ok = true;
                 const uint32_t iD = ptx::idesc_bf16(128, NCOL), iX = ptx::idesc_bf16(128, NXI);
-                for (uint32_t k = 0; k < U && ok; ++k) {
-                    const int st = ipos.st;
-                    if (!ptx::mbar_wait(&bars[st], ipos.ph, kSpin)) { ok = false; break; }
+                // two units at a time (a D unit and a Dx unit): their MMAs
+                // alternate between the two accumulators
+                for (uint32_t k = 0; k < U && ok; k += 2) {
+                    RingPos pos[2];
+                    pos[0] = ipos;
+                    advance<H>(ipos);
+                    pos[1] = ipos;
+                    advance<H>(ipos);
+                    uint32_t d_col[2], idesc[2];
+                    uint64_t a0[2], b0[2];
+                    bool first[2];
+                    for (int j = 0; j < 2; ++j) {
+                        if (!ptx::mbar_wait(&bars[pos[j].st], pos[j].ph, kSpin)) { ok = false; break; }
+                        const Unit u = unit_of<H>(l, (int)k + j);
+                        const bool dx = u.which >= 2;
+                        const uint32_t b_addr = dx ? ptx::smem_u32(sm + L::XI_OFF + u.s * L::XI_SLICE)
+                                                   : ptx::smem_u32(sm + L::XB_OFF + u.s * L::XB_SLICE);
+                        d_col[j] = tmem + (uint32_t)(u.m * 128 + (dx ? NCOL : 0));
+                        idesc[j] = dx ? iX : iD;
+                        first[j] = (u.which & 1) == 0 && u.s == 0;
+                        a0[j] = ptx::desc_kmajor_sw128(ptx::smem_u32(sm + L::RING_OFF + pos[j].st * TILE));
+                        b0[j] = ptx::desc_kmajor_sw128(b_addr);
+                    }
+                    if (!ok) break;
                     ptx::tc_fence_after();
-                    const Unit u = unit_of<H>(l, (int)k);
-                    const bool dx = u.which >= 2;
-                    const uint32_t b_addr = dx ? ptx::smem_u32(sm + L::XI_OFF + u.s * L::XI_SLICE)
-                                               : ptx::smem_u32(sm + L::XB_OFF + u.s * L::XB_SLICE);
-                    const uint32_t d_col = tmem + (uint32_t)(u.m * 128 + (dx ? NCOL : 0));
-                    const uint32_t idesc = dx ? iX : iD;
-                    const bool first = (u.which & 1) == 0 && u.s == 0;
-                    const uint64_t a0 = ptx::desc_kmajor_sw128(ptx::smem_u32(sm + L::RING_OFF + st * TILE));
-                    const uint64_t b0 = ptx::desc_kmajor_sw128(b_addr);
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
-                        ptx::mma_bf16(d_col, a0 + 2 * ks, b0 + 2 * ks, idesc, (first && ks == 0) ? 0u : 1u);
-                    ptx::mma_commit(&bars[L::NSTG + st]);
-                    if (k + 1 == U) ptx::mma_commit(acc_bar);
-                    advance<H>(ipos);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j)
+                            ptx::mma_bf16(d_col[j], a0[j] + 2 * ks, b0[j] + 2 * ks, idesc[j],
+                                          (first[j] && ks == 0) ? 0u : 1u);
+                    ptx::mma_commit(&bars[L::NSTG + pos[0].st]);
+                    ptx::mma_commit(&bars[L::NSTG + pos[1].st]);
+                    if (k + 2 == U) ptx::mma_commit(acc_bar);
                 }
                 *consumed += U;  // published once per layer for the exit drain
                 *issue_pos = ipos;
