@@ -332,7 +332,11 @@ def cast_frustum(net, eye, dirs, width, height, grid=16, opts=None, **kw):
 
 
 def cast_rays(net, origins, dirs, opts=None, t_hit=None, iters=None, **kw):
-    """Proc. 2 per ray; returns (t_hit float32 [n], iters int32 [n])."""
+    """Proc. 2 per ray; returns (t_hit float32 [n], iters int32 [n]).
+
+    precision "fp32" / "fp64" (SIMT) or "bf16" (tensor-core hidden layers);
+    recheck=True marches again in FP64 every ray that met a segment bound
+    within recheck_band of zero (recheck_count counts them)."""
     opts = opts or make_opts(**kw)
     _need(origins, torch.float32, 3, "origins")
     _need(dirs, torch.float32, 3, "dirs")
