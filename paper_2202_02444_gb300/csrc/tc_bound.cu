@@ -773,6 +773,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 if (i < NPART) {
                     for (int s = pp; s < Lt::S; s += NPART) {
                         const unsigned char *XC = x.smem + Lt::XC_OFF + s * Lt::XC_SLICE;
+#pragma unroll 8
                         for (int j = 0; j < 64; ++j) {
                             const float w = wout[s * 64 + j];
                             const float hi = __bfloat162float(
@@ -788,6 +789,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                     E[pp * (KT + 2) + KT] = err;
                 } else {
                     const float *xr = (const float *)(x.smem + Lt::XR_OFF) + g * H;
+#pragma unroll 8
                     for (int j = pp * (H / NPART); j < (pp + 1) * (H / NPART); ++j) acc = ru_fma(fabsf(wout[j]), xr[j], acc);
                     Y[pp * (KT + 2) + KT + 1] = acc;
                 }
@@ -795,8 +797,10 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             group_sync(g, H);
             if (i == 32 * g && bi < n) {  // lane 0 of warp g of the group (warps 0 and H/32 + 1)
                 float rad = 0.f, esum = 0.f, y0 = 0.f, ey = 0.f, yinf = 0.f;
+#pragma unroll 8
                 for (int k = 0; k < KT; ++k) {
                     float yk = 0.f, ek = 0.f;
+#pragma unroll 8
                     for (int pp = 0; pp < NPART; ++pp) {
                         yk += Y[pp * (KT + 2) + k];
                         ek = ru_add(ek, E[pp * (KT + 2) + k]);
