@@ -88,6 +88,13 @@ __device__ __forceinline__ void group_sync(int g, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(nthreads) : "memory");
 }
 
+// Warp-wide sum rounded up at every step (every lane gets the same value).
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -767,40 +774,49 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 Y[pp * (KT + 2) + k] = acc;
                 E[pp * (KT + 2) + k] = err;
             }
-            if (i < 2 * NPART) {  // center (c_hi + c_lo rows) and x_inf parts
-                const int pp = i % NPART;
-                float acc = 0.f, err = 0.f;
-                if (i < NPART) {
-                    for (int s = pp; s < Lt::S; s += NPART) {
-                        const unsigned char *XC = x.smem + Lt::XC_OFF + s * Lt::XC_SLICE;
-#pragma unroll 8
-                        for (int j = 0; j < 64; ++j) {
-                            const float w = wout[s * 64 + j];
-                            const float hi = __bfloat162float(
-                                *(const __nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g), (uint32_t)j)));
-                            const float lo = __bfloat162float(
-                                *(const __nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g + 1), (uint32_t)j)));
-                            acc = fmaf(w, hi, acc);
-                            acc = fmaf(w, lo, acc);
-                            err = ru_fma(fabsf(w), ru_add(fabsf(hi), fabsf(lo)), err);
-                        }
+            // center (c_hi + c_lo rows) and x_inf parts: warp wg < NPART takes
+            // part wg, its lanes split the inputs, warp reductions (rounded up
+            // for the error and x_inf sums)
+            if (x.wg < NPART) {
+                const int pp = x.wg, lane = x.lane;
+                float acc = 0.f, err = 0.f, xacc = 0.f;
+                for (int s = pp; s < Lt::S; s += NPART) {
+                    const unsigned char *XC = x.smem + Lt::XC_OFF + s * Lt::XC_SLICE;
+#pragma unroll
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const int j = lane + 32 * jj;
+                        const float w = wout[s * 64 + j];
+                        const float hi = __bfloat162float(
+                            *(const __nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g), (uint32_t)j)));
+                        const float lo = __bfloat162float(
+                            *(const __nv_bfloat16 *)(XC + ptx::sw128_offset((uint32_t)(2 * g + 1), (uint32_t)j)));
+                        acc = fmaf(w, hi, acc);
+                        acc = fmaf(w, lo, acc);
+                        err = ru_fma(fabsf(w), ru_add(fabsf(hi), fabsf(lo)), err);
                     }
+                }
+                const float *xr = (const float *)(x.smem + Lt::XR_OFF) + g * H;
+                for (int j = pp * (H / NPART) + lane; j < (pp + 1) * (H / NPART); j += 32)
+                    xacc = ru_fma(fabsf(wout[j]), xr[j], xacc);
+                acc = warp_sum_f(acc);
+                err = warp_sum_ru(err);
+                xacc = warp_sum_ru(xacc);
+                if (lane == 0) {
                     Y[pp * (KT + 2) + KT] = acc;
                     E[pp * (KT + 2) + KT] = err;
-                } else {
-                    const float *xr = (const float *)(x.smem + Lt::XR_OFF) + g * H;
-#pragma unroll 8
-                    for (int j = pp * (H / NPART); j < (pp + 1) * (H / NPART); ++j) acc = ru_fma(fabsf(wout[j]), xr[j], acc);
-                    Y[pp * (KT + 2) + KT + 1] = acc;
+                    Y[pp * (KT + 2) + KT + 1] = xacc;
                 }
             }
             group_sync(g, H);
-            if (i == 32 * g && bi < n) {  // lane 0 of warp g of the group (warps 0 and H/32 + 1)
+            // final sums by warp g of the group (warps 0 and H/32 + 1), two noise
+            // columns per lane; the radius and error sums are rounded up in
+            // any order, and the FP32 error factors gam_out / gam_c_out bound
+            // sequential summation, hence every other order too
+            if (x.wg == g && bi < n) {
                 float rad = 0.f, esum = 0.f, y0 = 0.f, ey = 0.f, yinf = 0.f;
-#pragma unroll 8
-                for (int k = 0; k < KT; ++k) {
+                for (int k = x.lane; k < KT; k += 32) {
                     float yk = 0.f, ek = 0.f;
-#pragma unroll 8
+#pragma unroll
                     for (int pp = 0; pp < NPART; ++pp) {
                         yk += Y[pp * (KT + 2) + k];
                         ek = ru_add(ek, E[pp * (KT + 2) + k]);
@@ -808,26 +824,30 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                     rad = ru_add(rad, fabsf(yk));
                     esum = ru_add(esum, ek);
                 }
-                for (int pp = 0; pp < NPART; ++pp) {
-                    y0 += Y[pp * (KT + 2) + KT];
-                    ey = ru_add(ey, E[pp * (KT + 2) + KT]);
-                    yinf = ru_add(yinf, Y[pp * (KT + 2) + KT + 1]);
-                }
-                y0 += p.bout;
-                ey = ru_add(ey, fabsf(p.bout));
-                rad = ru_add(rad, yinf);
-                if (SOUND) {
-                    rad = ru_fma(esum, p.gam_out, rad);  // noise-column sums (incl. the part adds)
-                    rad = ru_fma(ey, p.gam_c_out, rad);  // center sum, part adds and bias add
-                }
-                const float lo = rd_add(y0, -rad), hi = ru_add(y0, rad);
-                const int k = lo > 0.f ? SRA_POSITIVE : (hi < 0.f ? SRA_NEGATIVE : SRA_UNKNOWN);
-                if (out.lo) out.lo[bi] = lo;
-                if (out.hi) out.hi[bi] = hi;
-                if (out.cls) out.cls[bi] = (uint8_t)k;
-                if (out.flag_list) {
-                    const float band = out.band * (fabsf(y0) + rad);
-                    if (fabsf(lo) <= band || fabsf(hi) <= band) out.flag_list[atomicAdd(out.flag_count, 1)] = (int)bi;
+                rad = warp_sum_ru(rad);
+                esum = warp_sum_ru(esum);
+                if (x.lane == 0) {
+                    for (int pp = 0; pp < NPART; ++pp) {
+                        y0 += Y[pp * (KT + 2) + KT];
+                        ey = ru_add(ey, E[pp * (KT + 2) + KT]);
+                        yinf = ru_add(yinf, Y[pp * (KT + 2) + KT + 1]);
+                    }
+                    y0 += p.bout;
+                    ey = ru_add(ey, fabsf(p.bout));
+                    rad = ru_add(rad, yinf);
+                    if (SOUND) {
+                        rad = ru_fma(esum, p.gam_out, rad);  // noise-column sums (incl. the part adds)
+                        rad = ru_fma(ey, p.gam_c_out, rad);  // center sum, part adds and bias add
+                    }
+                    const float lo = rd_add(y0, -rad), hi = ru_add(y0, rad);
+                    const int k = lo > 0.f ? SRA_POSITIVE : (hi < 0.f ? SRA_NEGATIVE : SRA_UNKNOWN);
+                    if (out.lo) out.lo[bi] = lo;
+                    if (out.hi) out.hi[bi] = hi;
+                    if (out.cls) out.cls[bi] = (uint8_t)k;
+                    if (out.flag_list) {
+                        const float band = out.band * (fabsf(y0) + rad);
+                        if (fabsf(lo) <= band || fabsf(hi) <= band) out.flag_list[atomicAdd(out.flag_count, 1)] = (int)bi;
+                    }
                 }
             }
         }
