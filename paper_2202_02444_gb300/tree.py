@@ -10,11 +10,18 @@ checkpoint path continues from the last completed level instead of the root.
 The checkpoint records the problem it belongs to: the network's parameters
 (a SHA-1 of them), the depth, the root box and the options that change the
 tree. Resuming with a different problem is refused.
+
+Each level runs inside an NVTX range ("tree_level_<k>") for profilers, and
+with `log` set one JSON line per level is appended to that file: the level,
+its frontier size, the POSITIVE / NEGATIVE / UNKNOWN counts, the leaves and
+children it produced, the FP64 re-checks and the round's host time.
 """
 from __future__ import annotations
 
 import hashlib
+import json
 import os
+import time
 
 import numpy as np
 import torch
@@ -56,7 +63,7 @@ def load_state(path, key):
 
 
 def build_tree(net, depth, opts=None, root_lo=(-1.0, -1.0, -1.0), root_hi=(1.0, 1.0, 1.0), checkpoint=None,
-               cap=1 << 22, on_level=None, **kw):
+               cap=1 << 22, on_level=None, log=None, **kw):
     """Proc. 3 to a fixed depth, one sra_classify_and_split round per level.
 
     Returns (leaves, counts): the UNKNOWN leaves (NODE_DTYPE records, in the
@@ -79,9 +86,20 @@ def build_tree(net, depth, opts=None, root_lo=(-1.0, -1.0, -1.0), root_hi=(1.0, 
     while level <= depth and len(frontier):
         if len(frontier) * fan > cap and level < depth:
             raise sra.SraError(sra.ECAPACITY, f"level {level + 1} frontier would exceed {cap} nodes")
+        t0 = time.perf_counter()
+        torch.cuda.nvtx.range_push(f"tree_level_{level}")
         fr = sra.nodes_to_tensor(frontier, dev)
         out, lv, cnt = sra.classify_and_split(net, fr, depth, root_lo, root_hi, opts=opts)
         c = cnt.cpu().numpy()
+        torch.cuda.nvtx.range_pop()
+        if log:
+            rec = {"level": level, "frontier": int(len(frontier)), "positive": int(c[sra.CNT_POSITIVE]),
+                   "negative": int(c[sra.CNT_NEGATIVE]), "unknown": int(c[sra.CNT_UNKNOWN]),
+                   "leaves": int(c[sra.CNT_LEAVES]), "children": int(c[sra.CNT_CHILDREN]),
+                   "rechecked": int(c[sra.CNT_RECHECKED]), "converged": int(c[sra.CNT_CONVERGED]),
+                   "ms": (time.perf_counter() - t0) * 1e3}
+            with open(log, "a") as f:
+                f.write(json.dumps(rec) + "\n")
         n_children, n_leaves = int(c[sra.CNT_CHILDREN]), int(c[sra.CNT_LEAVES])
         frontier = sra.tensor_to_nodes(out[:n_children]) if n_children else np.zeros(0, sra.NODE_DTYPE)
         if n_leaves:

@@ -2,6 +2,7 @@
 the state file on the CPU, and on the GPU a build interrupted after a level
 that resumes to the same leaves and counts as an uninterrupted build and as
 the one-call sra_extract_leaves."""
+import json
 import os
 
 import numpy as np
@@ -67,8 +68,18 @@ def test_interrupted_build_resumes_to_the_same_tree(modules, tmp_path, arith, K,
         with pytest.raises(Interrupt):
             tree.build_tree(net, depth, opts=opts, checkpoint=path, on_level=stop_at)
         assert tree.load_state(path, tree.problem_key(mlp, depth, opts, (-1.0,) * 3, (1.0,) * 3))[0] == depth // 2
-        leaves, counts = tree.build_tree(net, depth, opts=opts, checkpoint=path)
+        log = str(tmp_path / "levels.jsonl")
+        leaves, counts = tree.build_tree(net, depth, opts=opts, checkpoint=path, log=log)
         assert np.array_equal(leaves, full_leaves) and np.array_equal(counts, full_counts)
+        # the log holds the resumed levels only, each with consistent counts
+        recs = [json.loads(line) for line in open(log)]
+        assert [r["level"] for r in recs] == list(range(depth // 2, depth + 1))
+        for r in recs:
+            assert r["positive"] + r["negative"] + r["unknown"] == r["frontier"]
+        # without the convergence test every leaf comes from the last level,
+        # one of the resumed ones
+        assert sum(r["leaves"] for r in recs) == len(leaves)
+
         # the one-call tree on the device gives the same leaf set
         ref, _ = sra.extract_leaves(net, depth, opts=opts)
         ref_set = {tuple(r) for r in sra.tensor_to_nodes(ref).tolist()}
