@@ -3,6 +3,7 @@
 // fixed-depth tree build (Proc. 3). Every step of the path runs in the
 // kernels of this library.
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cmath>
@@ -190,10 +191,25 @@ struct Carve {
     }
 };
 
+// Allocation failures to inject (sra_test_fail_allocs): each device
+// allocation of an entry point takes one and fails as out of memory.
+std::atomic<int> g_fail_allocs{0};
+
+bool take_injected_failure() {
+    int v = g_fail_allocs.load();
+    while (v > 0 && !g_fail_allocs.compare_exchange_weak(v, v - 1)) {
+    }
+    return v > 0;
+}
+
 sra_status scratch_alloc(Scratch &s, size_t bytes, cudaStream_t st) {
     keep_pool_memory();
     s.st = st;
     if (bytes == 0) bytes = 256;
+    if (take_injected_failure()) {
+        s.p = nullptr;
+        return fail(SRA_ENOMEM, "cudaMallocAsync(%zu): injected allocation failure", bytes);
+    }
     cudaError_t e = cudaMallocAsync(&s.p, bytes, st);
     if (e != cudaSuccess) {
         s.p = nullptr;
@@ -587,6 +603,10 @@ sra_status sra_load_mlp(const sra_mlp_desc *d, sra_net **out) {
         double *b64 = (double *)(host.data() + off_b64[l]);
         for (int i = 0; i < o; ++i) b64[i] = (double)b[i];
         p += (size_t)in * o + o;
+    }
+    if (take_injected_failure()) {
+        delete n;
+        return fail(SRA_ENOMEM, "cudaMalloc(%zu): injected allocation failure", total);
     }
     cudaError_t e = cudaMalloc(&n->buf, total);
     if (e != cudaSuccess) {
@@ -1584,5 +1604,12 @@ extern "C" sra_status sra_sync_status(const sra_net *n, void *stream) {
             return fail(SRA_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (code %d)", h);
         }
     }
+    return SRA_OK;
+}
+
+extern "C" sra_status sra_test_fail_allocs(int32_t n) {
+    g_err.clear();
+    if (n < 0) return fail(SRA_EINVAL, "n < 0");
+    g_fail_allocs.store(n);
     return SRA_OK;
 }

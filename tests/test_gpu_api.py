@@ -70,3 +70,42 @@ def test_leaf_capacity_status(sra):
     torch.cuda.synchronize()
     assert code == sra.ECAPACITY and nl.value > 10
     net.close()
+
+
+def test_injected_allocation_failures(sra):
+    """An injected allocation failure (host-side, sra_test_fail_allocs) makes
+    the call that needed the allocation return SRA_ENOMEM; the same call then
+    succeeds and returns what an undisturbed call returns."""
+    lib = sra.library()
+    lib.sra_test_fail_allocs.argtypes = [C.c_int32]
+    lib.sra_test_fail_allocs.restype = C.c_int
+    assert lib.sra_test_fail_allocs(-1) == sra.EINVAL
+    mlp = wl.net_small_relu()
+    try:
+        assert lib.sra_test_fail_allocs(1) == sra.OK
+        with pytest.raises(sra.SraError) as e:
+            sra.Net(mlp)
+        assert e.value.code == sra.ENOMEM and b"injected" in lib.sra_last_error()
+        net = sra.Net(mlp)
+        c, h = wl.make_boxes(300, seed=4)
+        C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
+        o, d = wl.sphere_rays(24, seed=5, radius=2.0)
+        O_, D_ = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
+        root = sra.nodes_to_tensor(wl.root_node())
+        calls = {
+            "boxes (FP64 re-check scratch)": lambda: sra.bound_boxes(net, C_, H_, arith="fixed", recheck=True,
+                                                                     recheck_band=1e-2)[0],
+            "octree round": lambda: sra.classify_and_split(net, root, 4, arith="fixed")[2],
+            "rays": lambda: sra.cast_rays(net, O_, D_, arith="fixed", delta=1e-3)[0],
+        }
+        for name, call in calls.items():
+            ref = call().cpu().numpy()
+            assert lib.sra_test_fail_allocs(1) == sra.OK
+            with pytest.raises(sra.SraError) as e:
+                call()
+            assert e.value.code == sra.ENOMEM, name
+            again = call().cpu().numpy()
+            assert np.array_equal(again.view(np.uint8), ref.view(np.uint8)), name
+        net.close()
+    finally:
+        lib.sra_test_fail_allocs(0)
