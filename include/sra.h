@@ -254,8 +254,8 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * (its origin's sign too) and its t_hit and iters are the FP64 ones;
  * opts->recheck_count, if given, counts those rays. n is at most 2^31 - 1.
  * Uses stream-ordered scratch of 4 bytes per ray (8 with recheck).
- * Errors: SRA_EINVAL (delta <= 0, bad steps), SRA_EUNSUPPORTED, SRA_ECUDA.
- * Asynchronous. */
+ * Errors: SRA_EINVAL (delta <= 0, bad steps, n > 2^31 - 1), SRA_EUNSUPPORTED,
+ * SRA_ENOMEM (scratch), SRA_ECUDA. Asynchronous. */
 sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *origins,
                          const float *dirs, int64_t n, float *t_hit, int32_t *iters,
                          void *stream);
