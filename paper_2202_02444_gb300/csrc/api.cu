@@ -1601,6 +1601,8 @@ extern "C" sra_status sra_sync_status(const sra_net *n, void *stream) {
         SRA_CK(cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost));
         if (h != 0) {
             SRA_CK(cudaMemset(w, 0, sizeof(int)));
+            if (h >= 100)  // debug builds only (SRA_DEBUG_BOUNDS)
+                return fail(SRA_ECUDA, "a device index check of a tensor-core kernel failed (code %d)", h);
             return fail(SRA_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (code %d)", h);
         }
     }

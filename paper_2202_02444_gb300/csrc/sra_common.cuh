@@ -128,6 +128,22 @@ template <typename T> struct RaySlotState {
     int flag;  // a decision of this ray was near zero
 };
 
+// Debug builds (-DSRA_DEBUG_BOUNDS) check data-dependent indices of the
+// tensor-core kernels before use: an index outside [0, bound) skips the
+// access and records `code` (>= 100) in the kernel's status word, which
+// sra_sync_status reports, instead of faulting. Release builds compile the
+// checks away.
+__device__ __forceinline__ bool idx_ok(long long idx, long long bound, int *status, int code) {
+#ifdef SRA_DEBUG_BOUNDS
+    if (idx >= 0 && idx < bound) return true;
+    atomicCAS(status, 0, code);
+    return false;
+#else
+    (void)idx; (void)bound; (void)status; (void)code;
+    return true;
+#endif
+}
+
 // A march step whose decision the FP64 re-check takes again: the segment
 // bound [y0 - rad, y0 + rad] has an end within band (|y0| + rad) of zero, the
 // case where the rounding of a lower precision can flip the segment's class

@@ -107,6 +107,7 @@ struct Ctx {
     uint32_t tmem;
     uint64_t *bars;  // [0,1] full, [2,3] empty, [4] acc
     int *abort_flag;
+    int *status;     // device status word (bounded waits; debug index checks)
 };
 
 __device__ __forceinline__ void fail(const Ctx &x, const TcParams &p, int code) {
@@ -245,7 +246,10 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
         const unsigned m = __ballot_sync(0xffffffffu, kp);
         const unsigned mnew = m & __ballot_sync(0xffffffffu, valid && c >= Ncur);
         if (lane == 0) km[k] = m;
-        if (kp && c >= Ncur) newlist[nb + __popc(mnew & below)] = (base + __popc(m & below)) | ((c - Ncur) << 16);
+        if (kp && c >= Ncur) {
+            const int q = nb + __popc(mnew & below);
+            if (idx_ok(q, KT, x.status, 101)) newlist[q] = (base + __popc(m & below)) | ((c - Ncur) << 16);
+        }
         base += __popc(m);
         eqb += __popc(meq);
         nb += __popc(mnew);
@@ -280,6 +284,7 @@ __device__ __forceinline__ void fill_new_rows(const Ctx &x, int Ncur) {
         const int ent = newlist[q];
         const uint32_t row = (uint32_t)(g * KT + (ent & 0xffff));
         const int neuron = ent >> 16;
+        if (!idx_ok(ent & 0xffff, KT, x.status, 102) || !idx_ok(neuron, H, x.status, 103)) continue;
         uint4 val = make_uint4(0u, 0u, 0u, 0u);
         if ((neuron >> 3) == ch) {
             const float ga = score[Ncur + neuron];
@@ -512,7 +517,8 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
             const bool k = (byte >> r) & 1u;
             const uint32_t row = (uint32_t)(g * KT) + pre + (uint32_t)__popc(byte & below_r);
             pre += (uint32_t)__popc(byte);
-            const uint32_t addr = k ? xa + row * 128u + ((c16 ^ (row & 7u)) << 4) : dummy;
+            const bool in = idx_ok((long long)row - g * KT, KT, x.status, 104);
+            const uint32_t addr = (k && in) ? xa + row * 128u + ((c16 ^ (row & 7u)) << 4) : dummy;
             uint32_t R[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -543,6 +549,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     x.bars = (uint64_t *)(x.smem + Lt::BAR_OFF);
     uint32_t *tmem_slot = (uint32_t *)(x.smem + Lt::MISC_OFF);
     x.abort_flag = (int *)(x.smem + Lt::MISC_OFF + 4);
+    x.status = p.status;
     const int tid = x.tid, g = x.g, i = x.i;
     const int warp = tid >> 5;
     // M tile m's MMAs are issued by lane 0 of warp m of group m (warps 0 and
@@ -846,7 +853,10 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                     if (out.cls) out.cls[bi] = (uint8_t)k;
                     if (out.flag_list) {
                         const float band = out.band * (fabsf(y0) + rad);
-                        if (fabsf(lo) <= band || fabsf(hi) <= band) out.flag_list[atomicAdd(out.flag_count, 1)] = (int)bi;
+                        if (fabsf(lo) <= band || fabsf(hi) <= band) {
+                            const int q = atomicAdd(out.flag_count, 1);
+                            if (idx_ok(q, n, x.status, 105)) out.flag_list[q] = (int)bi;
+                        }
                     }
                 }
             }

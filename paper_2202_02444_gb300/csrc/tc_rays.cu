@@ -432,7 +432,10 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             if (done) {
                 p.t_hit[s.idx] = result;
                 if (p.iters) p.iters[s.idx] = s.iters;
-                if (p.flag_list && s.flag) p.flag_list[atomicAdd(p.flag_count, 1)] = (int)s.idx;
+                if (p.flag_list && s.flag) {
+                    const int q = atomicAdd(p.flag_count, 1);
+                    if (idx_ok(q, p.n, p.status, 106)) p.flag_list[q] = (int)s.idx;
+                }
                 s.idx = -1;
             }
         }
