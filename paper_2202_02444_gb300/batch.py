@@ -5,7 +5,7 @@ network. The children of network k land contiguously in the round's output
 buffer and are the next round's segment k directly (no gather).
 
 A network whose next frontier would exceed `cap` nodes stops there and is
-reported as truncated (the tree driver's frontier budget)."""
+reported as truncated (the frontier budget of build_trees)."""
 from __future__ import annotations
 
 import numpy as np
