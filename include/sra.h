@@ -435,8 +435,8 @@ sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, const sra_opts 
 /* Description of the last error on this thread ("" if none). */
 const char *sra_last_error(void);
 
-/* Fault injection for tests (the paper has no counterpart; Sec. 4's
- * queries assume allocation succeeds): the next n device allocations made by the
+/* Fault injection for tests (the paper has no counterpart): the next n
+ * device allocations made by the
  * entry points (stream-ordered scratch and network buffers) fail as if the
  * device were out of memory, so the calls that need them return SRA_ENOMEM
  * after releasing what they had taken. Host-side only: no GPU work is
