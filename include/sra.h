@@ -436,11 +436,10 @@ sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, const sra_opts 
 const char *sra_last_error(void);
 
 /* Fault injection for tests (the paper has no counterpart): the next n
- * device allocations made by the
- * entry points (stream-ordered scratch and network buffers) fail as if the
- * device were out of memory, so the calls that need them return SRA_ENOMEM
- * after releasing what they had taken. Host-side only: no GPU work is
- * involved. n = 0 cancels the injection.
+ * device allocations made by the entry points (stream-ordered scratch and
+ * network buffers) fail as if the device were out of memory, so the calls
+ * that need them return SRA_ENOMEM after releasing what they had taken.
+ * Host-side only: no GPU work is involved. n = 0 cancels the injection.
  * Errors: SRA_EINVAL for n < 0. */
 sra_status sra_test_fail_allocs(int32_t n);
 
