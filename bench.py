@@ -25,7 +25,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from paper_2202_02444_gb300 import workloads as wl  # noqa: E402
-from paper_2202_02444_gb300.shard import weak_shard  # noqa: E402
+from paper_2202_02444_gb300.shard import rank_batch, rank_ray_tile  # noqa: E402
 
 BOX_FLOP = None  # filled per net (algorithmic FLOP per box-bound eval)
 
@@ -113,6 +113,8 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-cap", type=int, default=100_000, help="frontier cap per net per level")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="oracle boxes for cpu_baseline")
+    ap.add_argument("--cpu-sample-1core", type=int, default=1024,
+                    help="oracle boxes for the one-core cpu_baseline figure (0: skip)")
     ap.add_argument("--ref-sample", type=int, default=256, help="oracle boxes per reference step")
     return ap.parse_args()
 
@@ -372,19 +374,29 @@ def make_frontier(sra, net, level, batch, opts):
     return fr, nk
 
 
-def cpu_baseline(mlp, fr_nodes, K, nsample):
-    """The FP64 oracle on a bounded sample of the same frontier (all host cores)."""
+def cpu_baseline(mlp, fr_nodes, K, nsample, nsample_1core):
+    """The FP64 oracle on a bounded sample of the same frontier, on all host
+    cores and, on a smaller sample, on one core."""
     import oracle
-    idx = wl.sample_rows(len(fr_nodes), nsample, seed=5)
-    nodes = fr_nodes[idx]
     onet = oracle.OracleNet(mlp)
-    t0 = time.perf_counter()
-    oracle.classify_nodes(onet, nodes, (-1, -1, -1), (1, 1, 1), oracle.OCTREE, "truncate", K=K)
-    dt = time.perf_counter() - t0
-    return {"value": len(nodes) / dt, "unit": "box-bound evals/s", "cores": oracle.max_threads(),
+
+    def timed(n, threads):
+        nodes = fr_nodes[wl.sample_rows(len(fr_nodes), n, seed=5)]
+        t0 = time.perf_counter()
+        oracle.classify_nodes(onet, nodes, (-1, -1, -1), (1, 1, 1), oracle.OCTREE, "truncate", K=K,
+                              nthreads=threads)
+        return len(nodes), time.perf_counter() - t0
+
+    n_all, dt = timed(nsample, 0)
+    line = {"value": n_all / dt, "unit": "box-bound evals/s", "cores": oracle.max_threads(),
             "kind": "oracle",
-            "sample": f"{len(nodes)} level-7 frontier nodes of the 3-[256]x8-1 ReLU net, "
+            "sample": f"{n_all} level-7 frontier nodes of the 3-[256]x8-1 ReLU net, "
                       f"affine-truncate K={K}, FP64, {dt:.1f} s"}
+    if nsample_1core > 0:
+        n1, dt1 = timed(nsample_1core, 1)
+        line["single_core"] = {"value": n1 / dt1, "unit": "box-bound evals/s", "cores": 1,
+                               "sample": f"{n1} nodes of the same frontier, {dt1:.1f} s"}
+    return line
 
 
 def run_reference(args):
@@ -454,8 +466,32 @@ def kernel_case(args):
     print("kernel case done", args.kernel_case, args.batch)
 
 
+def free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def spawn_ranks(args):
+    """--gpus N > 1 started without a launcher: run this script again under
+    torch.distributed.run with N local ranks (one per GPU) and return its exit
+    code; None when there is nothing to spawn."""
+    if args.gpus <= 1 or "WORLD_SIZE" in os.environ:
+        return None
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.abspath(__file__),
+           *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse_args()
+    rc = spawn_ranks(args)
+    if rc is not None:
+        sys.exit(rc)
     if args.kernel_case:
         kernel_case(args)
         return
@@ -482,15 +518,11 @@ def main():
     # the frontier (a bench input) comes from the FP32 octree of the network
     fr_all, n_real = make_frontier(sra, net_box, args.frontier_level, args.batch * world,
                                    sra.make_opts(arith="truncate", K=K))
-    a_, b_ = weak_shard(args.batch, rank)  # this rank's batch of the global frontier
-    fr = fr_all[a_:b_].contiguous()
+    fr = rank_batch(fr_all, args.batch, rank).contiguous()  # this rank's batch of the global frontier
     B = fr.shape[0]
     o, d = wl.camera_rays(1920, 1080)
     T = args.ray_tile
-    W_, H_ = 1920, 1080
-    x0 = W_ // 2 - T // 2 + rank * T
-    y0 = H_ // 2 - T // 2
-    sel = np.array([(y0 + j) * W_ + (x0 + i) for j in range(T) for i in range(T)])
+    sel = np.array(rank_ray_tile(1920, 1080, T, rank))
     ro = torch.from_numpy(o[sel]).to(dev)
     rd = torch.from_numpy(d[sel]).to(dev)
     R = len(sel)
@@ -760,7 +792,8 @@ def main():
         bound = "tensor"
     if rank == 0:
         try:
-            cpu = cpu_baseline(mlp_box, nodes_h[:max(1, min(B, n_real))], K, args.cpu_sample)
+            cpu = cpu_baseline(mlp_box, nodes_h[:max(1, min(B, n_real))], K, args.cpu_sample,
+                               args.cpu_sample_1core)
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             cpu = {"value": None, "error": str(e)[:200]}
         line = {

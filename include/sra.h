@@ -330,18 +330,23 @@ sra_status sra_empty_spheres(const sra_net *net, const sra_opts *opts, const flo
 sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, void *stream);
 
 /* Allocation-free variant of sra_classify_and_split (same arguments, same
- * results). The paper has no counterpart: it exists for callers that cannot
- * allocate device memory at all, such as code running inside a captured CUDA
- * graph whose memory plan is fixed, real-time loops that forbid allocator
- * calls and their implicit synchronisation on the hot path, or hosts that
- * give this library a pre-partitioned device without an allocator. The round's
- * scratch lives in a fixed file-scope device array of
- * SRA_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
- * the process exits; the call itself allocates nothing.
- * Limits: n_in <= SRA_NOALLOC_MAX_NODES, else SRA_EINVAL (nothing queued);
- * precision FP32 or FP64 (BF16_SOUND gives SRA_EUNSUPPORTED).
+ * results for the options it accepts). The paper has no counterpart: it
+ * exists for callers that cannot allocate device memory at all, such as
+ * real-time loops that forbid allocator calls and their implicit
+ * synchronisation on the hot path, or hosts that give this library a
+ * pre-partitioned device without an allocator. The round's scratch lives in
+ * a fixed file-scope device array of SRA_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits; the call itself
+ * allocates nothing.
+ * Limits: n_in <= SRA_NOALLOC_MAX_NODES, else SRA_EINVAL (nothing queued).
+ * Unsupported options, each SRA_EUNSUPPORTED (nothing queued): precision
+ * SRA_PREC_BF16_SOUND or SRA_PREC_BF16 (FP32 and FP64 only), and
+ * opts->converge (the convergence test of Proc. 3).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make it before any stream capture. All calls share
+ * (cudaGetSymbolAddress) and keeps it for the rest of the process; make that
+ * first call before any stream capture. The address is not looked up again,
+ * so after cudaDeviceReset (or any teardown of the device's primary context)
+ * this entry point must not be used in the same process. All calls share
  * the array, which keeps the previous call's contents (each call clears what
  * must start at zero): calls whose device work overlaps (other streams or
  * host threads) race on it, so serialise them. Asynchronous on `stream`. */
@@ -442,6 +447,17 @@ const char *sra_last_error(void);
  * Host-side only: no GPU work is involved. n = 0 cancels the injection.
  * Errors: SRA_EINVAL for n < 0. */
 sra_status sra_test_fail_allocs(int32_t n);
+
+/* Failure detection test (the paper has no counterpart): while spins > 0,
+ * every launch of the tensor-core bound kernel (SRA_PREC_BF16_SOUND /
+ * SRA_PREC_BF16 box bounds) runs with its weight copies switched off and a
+ * budget of `spins` iterations for each bounded mbarrier wait. Every wait on
+ * a weight stage then runs out with no copy and no MMA in flight; the kernel
+ * records the timeout, frees its TMEM and leaves without writing its boxes'
+ * results, and sra_sync_status reports SRA_ETIMEOUT. spins = 0 restores
+ * normal operation (the default). Host-side setting; no GPU fault involved.
+ * Errors: SRA_EINVAL for spins outside [0, 2^20]. */
+sra_status sra_test_tc_stall(int32_t spins);
 
 #ifdef __cplusplus
 }

@@ -19,8 +19,7 @@
  *   - CastRay:                             Proc. 2, App. B "Ray Casting"
  *   - BuildSpatialTree (fixed depth):      Proc. 3, Sec. 4.5, Sec. 4.7
  *
- * Readings taken where the paper is garbled or silent (each is listed in the
- * design notes of the repository):
+ * Readings taken where the paper is garbled or silent:
  *   R1 ReLU table: the third line's "delta" is gamma; u<=0 gives the zero map,
  *      l>=0 the identity.
  *   R2 ELU table: "x_l > 0" means l >= 0; r_l is the tangent intercept

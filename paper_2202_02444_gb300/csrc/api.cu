@@ -191,6 +191,10 @@ struct Carve {
     }
 };
 
+// Bounded-wait budget of the tensor-core bound kernel for tests
+// (sra_test_tc_stall): 0 = normal operation.
+std::atomic<int> g_test_tc_stall{0};
+
 // Allocation failures to inject (sra_test_fail_allocs): each device
 // allocation of an entry point takes one and fails as out of memory.
 std::atomic<int> g_fail_allocs{0};
@@ -295,7 +299,15 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
         long long grid = num_sms();
         if (grid > tiles) grid = tiles;
         if (grid < 1) grid = 1;
-        cudaError_t e = launch_tc_bound(n->tc_H, o->precision == SRA_PREC_BF16_SOUND, n->tcp, src, out, (int)grid, st);
+        const int stall = g_test_tc_stall.load();
+        cudaError_t e;
+        if (stall > 0) {  // sra_test_tc_stall: a copy of the parameters with the stall set
+            TcParams p = n->tcp;
+            p.test_stall = stall;
+            e = launch_tc_bound(n->tc_H, o->precision == SRA_PREC_BF16_SOUND, p, src, out, (int)grid, st);
+        } else {
+            e = launch_tc_bound(n->tc_H, o->precision == SRA_PREC_BF16_SOUND, n->tcp, src, out, (int)grid, st);
+        }
         if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core bound launch: %s", cudaGetErrorString(e));
     } else {
         r = run_bound(n, o, fp64, 3, src, out, count, st);
@@ -1606,6 +1618,13 @@ extern "C" sra_status sra_sync_status(const sra_net *n, void *stream) {
             return fail(SRA_ETIMEOUT, "a bounded wait of a tensor-core kernel ran out (code %d)", h);
         }
     }
+    return SRA_OK;
+}
+
+extern "C" sra_status sra_test_tc_stall(int32_t spins) {
+    g_err.clear();
+    if (spins < 0 || spins > (1 << 20)) return fail(SRA_EINVAL, "spins %d outside [0, 2^20]", spins);
+    g_test_tc_stall.store(spins);
     return SRA_OK;
 }
 

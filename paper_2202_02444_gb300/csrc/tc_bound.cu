@@ -596,10 +596,15 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     constexpr int PRODUCER = NT - 32;
     uint32_t gload = 0;
     int ld_layer = 1, ld_slice = 0;
+    // bounded-wait budget; a test setting (p.test_stall > 0) also switches the
+    // copies off, so that every wait on a full stage runs out with nothing in
+    // flight (no copy, no MMA) and the CTA leaves through its normal exit
+    const uint32_t spins = p.test_stall > 0 ? (uint32_t)p.test_stall : kSpin;
     auto issue_upto = [&](uint32_t target) {  // the producer thread
+        if (p.test_stall > 0) return;
         while (gload < target && gload < total_slices && !*x.abort_flag) {
             const uint32_t gg = gload, st = gg & 1u;
-            if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, kSpin)) { fail(x, p, 3); return; }
+            if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, spins)) { fail(x, p, 3); return; }
             unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
             ptx::mbar_arrive_expect_tx(&x.bars[st], Lt::STAGE);
             const CUtensorMap *mb = &p.wb[ld_layer - 1], *mr = &p.wr[ld_layer - 1];
@@ -615,8 +620,10 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
         }
     };
 
+    // every abort decision is taken on a barrier that ORs the threads' flags,
+    // so the whole CTA leaves together even if a wait ran out just after it
     for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        if (*x.abort_flag) break;
+        if (__syncthreads_or(*x.abort_flag != 0)) break;
         const long long bi = t * NB + g;
         // ---- the group's box ----------------------------------------------
         if (i == 0) {
@@ -664,8 +671,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
         for (int l = 1; l + 1 < p.L; ++l) {
             ptx::fence_proxy_async();  // operand writes -> async proxy
             ptx::tc_fence_before();    // previous TMEM reads done before new MMAs
-            __syncthreads();
-            if (*x.abort_flag) break;
+            if (__syncthreads_or(*x.abort_flag != 0)) break;
             const float bias = p.b[l][i];  // read early: its latency hides under the MMA phase
             float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;  // rounded-up |W_b| v partials, boxes 0 and 1
             const uint32_t g0 = gring;
@@ -673,7 +679,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             const float *vg = (const float *)(x.smem + Lt::V_OFF) + g * H;
             for (int s = 0; s < Lt::S; ++s) {
                 const uint32_t gg = g0 + (uint32_t)s, st = gg & 1u, par = (gg >> 1) & 1u;
-                if (!ptx::mbar_wait(&x.bars[st], par, kSpin)) fail(x, p, 4);
+                if (!ptx::mbar_wait(&x.bars[st], par, spins)) fail(x, p, 4);
                 unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
                 if (issuer && !*x.abort_flag) {
                     ptx::tc_fence_after();
@@ -734,7 +740,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 if (tid == PRODUCER) issue_upto(g0 + (uint32_t)s + 3);
             }
             gring = g0 + Lt::S;
-            if (!ptx::mbar_wait(&x.bars[4], accn & 1u, kSpin)) fail(x, p, 5);
+            if (!ptx::mbar_wait(&x.bars[4], accn & 1u, spins)) fail(x, p, 5);
             accn++;
             if (tid == PRODUCER) issue_upto(gring + 2);  // next layer's (or tile's) first slices, during the epilogue
             // the other group's box: hand over this thread's half of its |W_b| v
@@ -742,15 +748,13 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             const float xown = ru_add(g == 0 ? xa0 : xb0, g == 0 ? xa1 : xb1);
             xp[(1 - g) * H + i] = ru_add(g == 0 ? xb0 : xa0, g == 0 ? xb1 : xa1);
             ptx::tc_fence_after();
-            __syncthreads();  // every operand read of this layer is done
-            if (*x.abort_flag) break;
+            if (__syncthreads_or(*x.abort_flag != 0)) break;  // every operand read of this layer is done
             // ---- epilogue of the group's box -------------------------------
             const float xacc = ru_add(xown, xp[g * H + i]);
             hidden_epilogue<H, SOUND>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
                                       tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
         }
-        __syncthreads();
-        if (*x.abort_flag) break;
+        if (__syncthreads_or(*x.abort_flag != 0)) break;
         // ---- output layer (H -> 1) on the SIMT cores ------------------------------
         {
             float *Y = (float *)(x.smem + Lt::OUT_OFF) + g * NPART * (KT + 2);  // [NPART][KT+2]

@@ -11,6 +11,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def run(env_extra, *args):
     env = dict(os.environ, **env_extra)
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "MASTER_ADDR", "MASTER_PORT"):
+        if k not in env_extra:
+            env.pop(k, None)
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", *args],
                        capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -34,3 +37,14 @@ def test_reference_line_follows_the_contract():
 def test_other_ranks_do_no_work():
     out = run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "1", "--warmup", "0")
     assert out.strip() == ""
+
+
+def test_gpus_flag_starts_one_rank_per_gpu():
+    """`--gpus 2` without a launcher re-runs the script under
+    torch.distributed.run with two ranks; rank 0 alone prints the line and
+    reports both ranks."""
+    out = run({}, "--gpus", "2", "--steps", "1", "--warmup", "0", "--ref-sample", "4")
+    lines = [l for l in out.strip().splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2

@@ -10,7 +10,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_2202_02444_gb300.shard import shard_range, weak_shard
+from paper_2202_02444_gb300.shard import rank_batch, rank_ray_tile, shard_range, weak_shard
 
 
 def _free_port():
@@ -28,9 +28,14 @@ def _worker(rank, world, port, n, q):
     try:
         import oracle
         from paper_2202_02444_gb300 import workloads as wl
+        # the benchmark's split: the frontier is tiled to n_per_rank * world
+        # nodes and every rank bounds its own fixed-size batch (rank_batch)
         nodes = wl.random_nodes(n, level=4, seed=12)
-        a, b = shard_range(n, rank, world)
-        cls, lo, hi, _ = oracle.classify_nodes(wl.net_small_relu(), nodes[a:b], (-1, -1, -1), (1, 1, 1),
+        n_per_rank = (n + world - 1) // world
+        tiled = np.concatenate([nodes] * 2)[:n_per_rank * world]
+        mine = rank_batch(tiled, n_per_rank, rank)
+        a, b = weak_shard(n_per_rank, rank)
+        cls, lo, hi, _ = oracle.classify_nodes(wl.net_small_relu(), mine, (-1, -1, -1), (1, 1, 1),
                                                nthreads=1)
         tally = torch.tensor([(cls == k).sum() for k in (0, 1, 2)], dtype=torch.int64)
         dist.all_reduce(tally, op=dist.ReduceOp.SUM)
@@ -73,7 +78,16 @@ def test_two_process_tallies_merge():
     tally, sizes, tmax = q.get(timeout=10)
     import oracle
     from paper_2202_02444_gb300 import workloads as wl
-    cls, *_ = oracle.classify_nodes(wl.net_small_relu(), wl.random_nodes(n, level=4, seed=12),
-                                    (-1, -1, -1), (1, 1, 1))
+    n_per_rank = (n + world - 1) // world
+    tiled = np.concatenate([wl.random_nodes(n, level=4, seed=12)] * 2)[:n_per_rank * world]
+    cls, *_ = oracle.classify_nodes(wl.net_small_relu(), tiled, (-1, -1, -1), (1, 1, 1))
     assert tally == [int((cls == k).sum()) for k in (0, 1, 2)]
-    assert sum(sizes) == n and tmax == 2.0
+    assert sum(sizes) == n_per_rank * world and tmax == 2.0
+
+
+def test_rank_ray_tiles_are_disjoint():
+    tiles = [set(rank_ray_tile(1920, 1080, 64, r)) for r in range(8)]
+    assert all(len(t) == 64 * 64 for t in tiles)
+    assert len(set().union(*tiles)) == 8 * 64 * 64
+    with pytest.raises(ValueError):
+        rank_ray_tile(1920, 1080, 64, 20)

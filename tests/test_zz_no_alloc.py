@@ -1,13 +1,14 @@
 """The allocation-free octree round (sra_classify_and_split_noalloc).
 
-Some callers of this library cannot allocate device memory: code inside a
-captured CUDA graph with a fixed memory plan, real-time loops that forbid
-allocator calls on the hot path, or hosts that hand over a pre-partitioned
-device. For them the round keeps its scratch in a fixed device array. This
-test calls the variant through the C ABI and checks that it returns exactly
-what the allocating entry point returns, twice in a row (the array keeps the
-previous call's contents, so the second call must not depend on them).
-The file is named to be collected last.
+Some callers of this library cannot allocate device memory: real-time loops
+that forbid allocator calls on the hot path, or hosts that hand over a
+pre-partitioned device without an allocator. For them the round keeps its
+scratch in a fixed device array. This test calls the variant through the C
+ABI and checks that it returns exactly what the allocating entry point
+returns, twice in a row (the array keeps the previous call's contents, so the
+second call must not depend on them), while every allocation the library
+would make is set to fail (a host-side injection: an allocation would turn
+into SRA_ENOMEM). The file is named to be collected last.
 """
 import ctypes as C
 
@@ -50,7 +51,12 @@ def test_noalloc_round_equals_allocating_round(sra, recheck):
     for seed, level, max_level in ((9, 5, 6), (10, 6, 6)):  # two calls in a row
         fr = sra.nodes_to_tensor(wl.random_nodes(50000 + seed, level=level, seed=seed))
         c0, o0, l0, n0 = round_via(sra, lib.sra_classify_and_split, net, fr, max_level, opts)
-        c1, o1, l1, n1 = round_via(sra, lib.sra_classify_and_split_noalloc, net, fr, max_level, opts)
+        # any device allocation of the library would now fail with SRA_ENOMEM
+        assert lib.sra_test_fail_allocs(1000) == 0
+        try:
+            c1, o1, l1, n1 = round_via(sra, lib.sra_classify_and_split_noalloc, net, fr, max_level, opts)
+        finally:
+            lib.sra_test_fail_allocs(0)
         assert c0 == 0 and c1 == 0, lib.sra_last_error()
         assert torch.equal(n0, n1)
         assert torch.equal(o0, o1) and torch.equal(l0, l1)
@@ -67,4 +73,15 @@ def test_noalloc_rejects_oversized_input(sra):
     code, *_ = round_via(sra, lib.sra_classify_and_split_noalloc, net, fr, 3, opts)
     assert code == sra.EINVAL
     assert b"allocation-free limit" in lib.sra_last_error()
+    net.close()
+
+
+@pytest.mark.parametrize("what", ["bf16_sound", "bf16", "converge"])
+def test_noalloc_rejects_unsupported_options(sra, what):
+    lib = sra.library()
+    net = sra.Net(wl.net_small_relu())
+    opts = sra.make_opts(converge=True) if what == "converge" else sra.make_opts(precision=what)
+    fr = sra.nodes_to_tensor(wl.random_nodes(64, level=3, seed=3))
+    code, *_ = round_via(sra, lib.sra_classify_and_split_noalloc, net, fr, 4, opts)
+    assert code == sra.EUNSUPPORTED
     net.close()
