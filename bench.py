@@ -111,6 +111,7 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-octree", action="store_true", help="skip the depth-10 octree builds")
     ap.add_argument("--batched-cap", type=int, default=100_000, help="frontier cap per net per level")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="oracle boxes for cpu_baseline")
     ap.add_argument("--cpu-sample-1core", type=int, default=1024,
@@ -358,6 +359,59 @@ def policies_phase(sra, torch, dev):
                                               "affine-full": 96.4, "hardware": "RTX 2070, JAX"}
     net.close()
     return res
+
+
+def octree_phase(sra, torch, dev, net, depth=10, level_cap=1 << 21, K=64):
+    """The whole octree of the 3-[256]x8-1 ReLU net to depth 10 (Proc. 3),
+    level by level from the root, in FP32, and in plain BF16 and BF16-sound
+    (tensor cores) with the FP64 re-check: each level's frontier is bounded in chunks of at most
+    `level_cap` nodes (one sra_classify_and_split call each); a level whose
+    frontier exceeds `level_cap` nodes ends the build. Per level: the frontier,
+    the class counts and the device time of its rounds (CUDA events)."""
+    forms = {"fp32": sra.make_opts(arith="truncate", K=K),
+             "bf16": sra.make_opts(arith="truncate", K=K, precision="bf16", recheck=True, recheck_band=1e-5),
+             "bf16_sound": sra.make_opts(arith="truncate", K=K, precision="bf16_sound", recheck=True,
+                                         recheck_band=1e-5)}
+    out = {"workload": f"octree of ReLU 3-[256]x8-1 (seed 1) over [-1,1]^3 to depth {depth}, affine-truncate "
+                       f"K={K}; a level's frontier is bounded in chunks and may hold at most {level_cap} nodes",
+           "forms": {}}
+    buf = [torch.empty((8 * level_cap, 4), dtype=torch.int16, device=dev) for _ in range(2)]
+    leaves = torch.empty((level_cap, 4), dtype=torch.int16, device=dev)
+    counts = torch.zeros(8, dtype=torch.int64, device=dev)
+    for name, o in forms.items():
+        fr = sra.nodes_to_tensor(wl.root_node(), device=dev)
+        levels, total_ms, evals, stop = [], 0.0, 0, None
+        for level in range(depth + 1):
+            n = fr.shape[0]
+            if n == 0:
+                break
+            if n > level_cap:
+                stop = f"level {level} frontier of {n} nodes exceeds {level_cap}"
+                break
+            nxt = buf[level % 2]
+            counts.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sra.classify_and_split(net, fr, depth, opts=o, out=nxt, leaves=leaves, counts=counts)
+            e1.record()
+            torch.cuda.synchronize()
+            sra.sync_status(net)
+            ms = e0.elapsed_time(e1)
+            c = counts.cpu().numpy()
+            total_ms += ms
+            evals += n
+            levels.append({"level": level, "frontier": n, "pos": int(c[2]), "neg": int(c[3]), "unk": int(c[4]),
+                           "leaves": int(c[1]), "rechecked": int(c[5]), "ms": ms})
+            kids = int(c[0])
+            fr = nxt[:min(kids, nxt.shape[0])]
+            if kids > nxt.shape[0]:
+                stop = f"level {level + 1} frontier of {kids} nodes exceeds {nxt.shape[0]}"
+                break
+        out["forms"][name] = {"levels": levels, "box_evals": evals, "device_ms": total_ms,
+                              "box_evals_per_s": evals / (total_ms / 1e3) if total_ms > 0 else None,
+                              "completed": stop is None, "stopped": stop,
+                              "leaves_at_depth": levels[-1]["leaves"] if stop is None and levels else None}
+    return out
 
 
 def make_frontier(sra, net, level, batch, opts):
@@ -671,7 +725,11 @@ def main():
         completion = {"rays": int(nc), "form": "bf16", "cap": args.ray_complete_cap, "ms": c_ms,
                       "completed": int(ended.sum()), "hits": int(np.isfinite(t_c).sum()),
                       "rays_per_s": float(ended.sum()) / (c_ms / 1e3),
-                      "iters_per_completed_ray": it_mean}
+                      "iters_per_completed_ray": it_mean,
+                      "frame_fraction": nc / (1920 * 1080),
+                      "frame_estimate_s": (1920 * 1080) / max(float(ended.sum()) / (c_ms / 1e3), 1e-30),
+                      "frame_note": "the 1920x1080 frame (2,073,600 rays) at this sample's completed-ray rate; "
+                                    "the sample is one wave of central rays"}
         for form, rf in ray_forms.items():
             rf["rays_per_s_at_sample_iters"] = rf["ray_iters_per_s"] / it_mean if ended.any() else None
     ta, tb = ray_t["fp32"], ray_t["bf16"]
@@ -759,6 +817,7 @@ def main():
                    "decided_frac": float((rad > 0).float().mean()), "median_radius": float(rad.median())}
 
     policies = policies_phase(sra, torch, dev) if rank == 0 else None
+    octree = octree_phase(sra, torch, dev, net_box) if rank == 0 and not args.no_octree else None
 
     batched = None
     if not args.no_batched and rank == 0:
@@ -835,6 +894,7 @@ def main():
             "empty_spheres": spheres,
             "frustum": frustum,
             "policies": policies,
+            "octree_depth10": octree,
             "batched": batched,
             "serving": serving,
             "cpu_baseline": cpu,

@@ -15,6 +15,7 @@ import torch
 import oracle
 from paper_2202_02444_gb300 import workloads as wl
 from tests.np_forward import box_samples, forward
+from tests.sound_emulation import bound as emulate
 
 pytestmark = pytest.mark.gpu
 
@@ -85,6 +86,45 @@ def test_bf16_vs_oracle_excess(sra):
     print(f"bf16 radius excess over FP64: median {np.median(excess):.4g} max {excess.max():.4g}; "
           f"classes equal {np.mean(cls == ref['cls']):.3f}")
     assert np.all(excess > -1e-6)
+    net.close()
+
+
+SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
+           "relu256x3": lambda: wl.make_mlp([256] * 3, "relu", seed=32)}
+
+
+@pytest.mark.parametrize("name", list(SHALLOW))
+def test_bf16_sound_classes_on_shallow_nets(sra, name):
+    """Where the |W| amplification of the a-priori rounding radius is small
+    (two tensor-core layers), the sound form decides nearly everything the
+    oracle decides. Gates: the sound bound contains the oracle's (boxes whose
+    truncation had a near-tie exempt); no decided class contradicts the
+    oracle; and the boxes the oracle decides but the sound form leaves UNKNOWN
+    are no more than an FP64 model of the sound form's arithmetic predicts
+    (tests/sound_emulation.py: per dense layer an a-priori product and
+    accumulation error u per unit of |W| (|c| + |A|), u = 2^-16 + 17 * (2H/16)
+    * 2^-23 * (1 + 2^-7); per activation the BF16 storage of the scaled noise
+    entries, 2^-8 of their magnitudes; both into x_inf), plus 1 % of the
+    decided boxes."""
+    mlp = SHALLOW[name]()
+    net = sra.Net(mlp)
+    c, h = wl.make_boxes(1021, seed=7, hw_lo=1 / 256, hw_hi=1 / 16)
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
+    tie = ref["sel_gap"] < 1e-2
+    scale = np.abs(ref["y0"]) + ref["rad"]
+    slack = 1e-6 * scale
+    assert np.all(((lo <= ref["lo"] + slack) & (hi >= ref["hi"] - slack)) | tie)
+    assert not np.any(((cls == 1) & (ref["cls"] == 2)) | ((cls == 2) & (ref["cls"] == 1)))
+    H = mlp.widths[1]
+    u = (2.0 ** -16 + 17 * (2 * H // 16) * 2.0 ** -23 * (1 + 2.0 ** -7)) * 1.001
+    mcls = emulate(mlp, c, h, 64, "xinf", u, u_store=2.0 ** -8)[0]
+    dec = ref["cls"] != 0
+    lost, lost_model = dec & (cls == 0), dec & (mcls == 0)
+    print(f"{name}: oracle UNKNOWN {np.mean(~dec):.4f}, BF16-sound UNKNOWN {np.mean(cls == 0):.4f} "
+          f"(model {np.mean(mcls == 0):.4f}); decided by the oracle but not by BF16-sound {lost.sum()} "
+          f"(model {lost_model.sum()}) of {dec.sum()}")
+    assert lost.sum() <= lost_model.sum() + 0.01 * dec.sum()
     net.close()
 
 
