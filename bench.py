@@ -42,6 +42,18 @@ def box_flops(mlp, K):
     return f
 
 
+def full_flops(mlp):
+    """Affine-full: sum over linear layers of 2 * h_out * h_in * (symbols + 1),
+    the symbol count growing by h_out after every nonlinear layer."""
+    f, sym = 0, 3 + 6 * mlp.pe_octaves
+    for l in range(mlp.n_layers):
+        hin, hout = mlp.widths[l], mlp.widths[l + 1]
+        f += 2 * hout * hin * (sym + 1)
+        if l + 1 < mlp.n_layers:
+            sym += hout
+    return f
+
+
 def ray_iter_flops(mlp):
     """One CastRay iteration: segment bound (1 symbol + center + x_inf) plus
     the plain point evaluation, through every linear layer."""
@@ -56,7 +68,7 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true>": {"sha1": "81ecc6ea115fbdaf2b5ad4f734a5461cc10afc82", "bytes": 3342592,
+    "tc_bound_kernel<256,true>": {"sha1": "de669634f5a833ec72e7eadb050ab01b365e8465", "bytes": 3328256,
                                   "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
@@ -357,6 +369,23 @@ def policies_phase(sra, torch, dev):
                                  "unknown_frac": float((cl == 0).float().mean())}
     res["paper_table1_3d_cost_vs_forward"] = {"interval": 2.3, "affine-fixed": 6.7, "affine-truncate": 69.0,
                                               "affine-full": 96.4, "hardware": "RTX 2070, JAX"}
+    net.close()
+    # the config-2 network: affine-full keeps 2051 symbols, each box's noise
+    # matrix in device memory (one batched GEMM per layer)
+    wide = wl.net_relu256x8()
+    net = sra.Net(wide)
+    Bw = 4096
+    c, h = wl.make_boxes(Bw, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
+    C_, H_ = torch.from_numpy(c).to(dev), torch.from_numpy(h).to(dev)
+    res["wide"] = {"workload": f"ReLU 3-[256]x8-1 (seed 1), {Bw} boxes, half-widths log-U[1/1024, 1/64], FP32",
+                   "policies": {}}
+    for name, arith, K in (("affine-truncate K=64", "truncate", 64), ("affine-full", "full", 0)):
+        o = sra.make_opts(arith=arith, K=K)
+        ms, (lo, hi, cl) = timed(lambda: sra.bound_boxes(net, C_, H_, opts=o))
+        flop = full_flops(wide) if arith == "full" else box_flops(wide, K)
+        res["wide"]["policies"][name] = {"box_evals_per_s": Bw / (ms / 1e3), "mean_width": float((hi - lo).mean()),
+                                         "unknown_frac": float((cl == 0).float().mean()),
+                                         "flop_per_box": flop, "tflops": flop * Bw / (ms / 1e3) / 1e12}
     net.close()
     return res
 

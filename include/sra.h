@@ -52,10 +52,14 @@ enum {
     SRA_ARITH_AFFINE_FIXED = 1,    /* keep only the input-domain symbols */
     SRA_ARITH_AFFINE_TRUNCATE = 2, /* keep the K largest symbols (column L1 norm) */
     SRA_ARITH_AFFINE_FULL = 3      /* keep every symbol: up to 128 symbols on every kernel; past
-                                      that, box bounds (sra_bound_boxes, sra_classify_and_split and
-                                      the entry points built on them) of networks of width <= 64
+                                      that, box bounds only (sra_bound_boxes, sra_classify_and_split
+                                      and the entry points built on them): networks of width <= 64
                                       without positional encoding whose state fits in shared memory
-                                      (e.g. 8-layer 32-wide: 227 symbols); else SRA_EUNSUPPORTED */
+                                      run one CTA per box (e.g. 8-layer 32-wide: 227 symbols); any
+                                      other network keeps each box's noise matrix in device memory
+                                      (stream-ordered scratch of up to 1 GiB per call, 2 * width *
+                                      (symbols + 1) floats per box; 3-[256]x8-1: 2051 symbols,
+                                      4.2 MB per box in FP32), the boxes taken in passes that fit */
 };
 
 /* Slope of the activation linearisation: Chebyshev (App. A) or min-range. */

@@ -241,18 +241,31 @@ void kd_tables(const float *lo, const float *hi, unsigned char n3[][3], unsigned
 
 // Launch RangeBound over a box source in FP32 or FP64: the SIMT engine, or,
 // for affine-full past its 128 register columns, the shared-memory full
-// kernel (widths up to 64, no positional encoding).
+// kernel (widths up to 64, no positional encoding, state within one CTA) or
+// else the full kernels with each box's noise matrix in device memory.
 sra_status run_bound(const sra_net *n, const sra_opts *o, bool fp64, int s, const BoxSrc &src,
                      const BoundOut &out, long long n_hint, cudaStream_t st) {
     if (o->arith == SRA_ARITH_AFFINE_FULL && s + n->new_syms > kKmaxList[sizeof kKmaxList / sizeof(int) - 1]) {
+        if (s != 3) return fail(SRA_EUNSUPPORTED, "affine-full with %d symbols runs on box bounds only", s + n->new_syms);
         FullCfg fc;
-        if (n->pe || s != 3 || full_cfg(n->rows, s + n->new_syms, o->slope, fp64 ? 8 : 4, &fc) != SRA_OK)
-            return fail(SRA_EUNSUPPORTED,
-                        "affine-full with %d symbols needs the shared-memory full kernel: box bounds of a "
-                        "network without positional encoding, widths <= %d, state within shared memory",
-                        s + n->new_syms, kFullMaxWidth);
-        cudaError_t e = launch_full_bound(fp64, n->dev, src, out, fc, n_hint, st);
-        if (e != cudaSuccess) return fail(SRA_ECUDA, "full bound kernel launch: %s", cudaGetErrorString(e));
+        if (!n->pe && full_cfg(n->rows, s + n->new_syms, o->slope, fp64 ? 8 : 4, &fc) == SRA_OK) {
+            cudaError_t e = launch_full_bound(fp64, n->dev, src, out, fc, n_hint, st);
+            if (e != cudaSuccess) return fail(SRA_ECUDA, "full bound kernel launch: %s", cudaGetErrorString(e));
+            return SRA_OK;
+        }
+        FullHbmCfg hc;
+        if (full_hbm_cfg(n->dev, n->rows, o->slope, fp64 ? 8 : 4, kFullHbmBudget, &hc) != SRA_OK)
+            return fail(SRA_EUNSUPPORTED, "affine-full state of one box exceeds %zu bytes", kFullHbmBudget / 2);
+        if (n_hint <= 0) return SRA_OK;
+        if (hc.chunk > n_hint) {  // one pass: scratch for the boxes there are
+            hc.bytes = hc.bytes / (size_t)hc.chunk * (size_t)n_hint;
+            hc.chunk = n_hint;
+        }
+        Scratch sc;
+        sra_status r = scratch_alloc(sc, hc.bytes, st);
+        if (r) return r;
+        cudaError_t e = launch_full_hbm(fp64, n->dev, hc, src, out, n_hint, sc.p, st);
+        if (e != cudaSuccess) return fail(SRA_ECUDA, "full (device-memory) kernel launch: %s", cudaGetErrorString(e));
         return SRA_OK;
     }
     int kmax = 0;
@@ -1538,6 +1551,11 @@ extern "C" sra_status sra_classify_and_split_noalloc(
     if (o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16)
         return fail(SRA_EUNSUPPORTED, "the allocation-free round runs in FP32 or FP64");
     if (o->converge) return fail(SRA_EUNSUPPORTED, "the allocation-free round has no convergence test");
+    if (o->arith == SRA_ARITH_AFFINE_FULL && 3 + n->new_syms > kKmaxList[sizeof kKmaxList / sizeof(int) - 1]) {
+        FullCfg fc;
+        if (n->pe || full_cfg(n->rows, 3 + n->new_syms, o->slope, o->precision == SRA_PREC_FP64 ? 8 : 4, &fc))
+            return fail(SRA_EUNSUPPORTED, "the allocation-free round has no affine-full state in device memory");
+    }
     void *scratch = nullptr;
     if ((r = noalloc_scratch(&scratch))) return r;  // before any early return for n_in == 0
     if (n_in == 0) return SRA_OK;

@@ -33,6 +33,23 @@ sra_status full_cfg(int rows, int total_syms, int slope, int tsize, FullCfg *fc)
 cudaError_t launch_full_bound(bool fp64, const NetDev &net, const BoxSrc &src, const BoundOut &out,
                               const FullCfg &fc, long long n_hint, cudaStream_t st);
 
+// Affine-full RangeBound with each box's noise matrix in device memory
+// (full_hbm.cu): any width, with or without positional encoding. A pass
+// takes `chunk` boxes; `bytes` of scratch hold two [rows][LD] noise matrices
+// and two FP64 center vectors [rows] per box.
+struct FullHbmCfg {
+    int rows;        // state rows: the largest layer width
+    int LD;          // row stride: 1 + symbols, rounded up to 4
+    int slope;       // SRA_SLOPE_*
+    int syms;        // symbols after the last nonlinearity
+    long long chunk; // boxes per pass
+    size_t bytes;    // scratch of one pass
+};
+constexpr size_t kFullHbmBudget = (size_t)1 << 30;  // scratch bytes of one pass
+sra_status full_hbm_cfg(const NetDev &net, int rows, int slope, int tsize, size_t budget, FullHbmCfg *fc);
+cudaError_t launch_full_hbm(bool fp64, const NetDev &net, const FullHbmCfg &fc, const BoxSrc &src,
+                            const BoundOut &out, long long n_hint, void *scratch, cudaStream_t st);
+
 struct RayParams;
 cudaError_t launch_rays_f32(int kmax, const NetDev &net, const void *rp, const RangeCfg &cfg,
                             int grid, cudaStream_t st);

@@ -76,11 +76,15 @@ def test_noalloc_rejects_oversized_input(sra):
     net.close()
 
 
-@pytest.mark.parametrize("what", ["bf16_sound", "bf16", "converge"])
+@pytest.mark.parametrize("what", ["bf16_sound", "bf16", "converge", "full_in_device_memory"])
 def test_noalloc_rejects_unsupported_options(sra, what):
     lib = sra.library()
-    net = sra.Net(wl.net_small_relu())
-    opts = sra.make_opts(converge=True) if what == "converge" else sra.make_opts(precision=what)
+    if what == "full_in_device_memory":  # a 128-wide net's full state needs device scratch
+        net = sra.Net(wl.make_mlp([128] * 3, "relu", seed=61))
+        opts = sra.make_opts(arith="full")
+    else:
+        net = sra.Net(wl.net_small_relu())
+        opts = sra.make_opts(converge=True) if what == "converge" else sra.make_opts(precision=what)
     fr = sra.nodes_to_tensor(wl.random_nodes(64, level=3, seed=3))
     code, *_ = round_via(sra, lib.sra_classify_and_split_noalloc, net, fr, 4, opts)
     assert code == sra.EUNSUPPORTED
