@@ -119,12 +119,12 @@ def parse_args():
     ap.add_argument("--kernel-case", default=None,
                     choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
-    ap.add_argument("--serve-rates", default="2,8", help="request rates (req/s) of the serving sweep")
+    ap.add_argument("--serve-rates", default="2,4,8,16", help="request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-octree", action="store_true", help="skip the depth-10 octree builds")
-    ap.add_argument("--batched-cap", type=int, default=100_000, help="frontier cap per net per level")
+    ap.add_argument("--batched-cap", type=int, default=500_000, help="frontier cap per net per level (the batched workload: frontiers of 1k-500k boxes per level)")
     ap.add_argument("--cpu-sample", type=int, default=16384, help="oracle boxes for cpu_baseline")
     ap.add_argument("--cpu-sample-1core", type=int, default=1024,
                     help="oracle boxes for the one-core cpu_baseline figure (0: skip)")
@@ -189,6 +189,14 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def tc_box_net(m):
+    """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU
+    network with one hidden width H in {128, 256} and at most 12 hidden
+    tensor-core layers, no positional encoding."""
+    return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and all(a == 1 for a in m.acts)
+            and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
 
 
 def serving_nets():
@@ -313,6 +321,26 @@ def batched_phase(sra, torch, cap):
     nodes = sum(r["nodes"] for r in res)
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
+    # the same 64 trees with BF16-sound bounds on the tensor cores for every
+    # network that has that kernel (ReLU, one width 128 or 256, K = 64), the
+    # others in their autotuned FP32 form, all in the same batched rounds
+    tc = [tc_box_net(m) for m in mlps]
+    opts_tc = [sra.make_opts(arith="truncate", K=64, precision="bf16_sound") if t else o for t, o in zip(tc, opts)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res_tc, rounds_tc = batch.build_trees(nets, opts_tc, depths, cap=cap)
+    torch.cuda.synchronize()
+    t_tc = time.perf_counter() - t0
+    for n, t in zip(nets, tc):
+        if t:
+            sra.sync_status(n)
+    nodes_tc = sum(r["nodes"] for r in res_tc)
+    flop_tc = sum(r["nodes"] * box_flops(m, 64 if t else u["K"]) for r, m, t, u in zip(res_tc, mlps, tc, tuned))
+    bf16_sound = {"nets_on_tensor_cores": int(sum(tc)), "box_evals": nodes_tc, "rounds": rounds_tc, "s": t_tc,
+                  "evals_per_s": nodes_tc / t_tc, "tflops": flop_tc / t_tc / 1e12,
+                  "tensor_core_box_evals": int(sum(r["nodes"] for r, t in zip(res_tc, tc) if t)),
+                  "nets_truncated_at_cap": int(sum(r["truncated"] for r in res_tc)),
+                  "tensor_core_nets_truncated_at_cap": int(sum(r["truncated"] for r, t in zip(res_tc, tc) if t))}
     for n in nets:
         n.close()
     ks = {}
@@ -326,7 +354,7 @@ def batched_phase(sra, torch, cap):
             "one_by_one_s": t1, "one_by_one_evals_per_s": nodes / t1,
             "batched_vs_one_by_one": t1 / tb, "same_trees": same,
             "nets_truncated_at_cap": int(sum(r["truncated"] for r in res)),
-            "autotune_s": t_tune, "autotune_K": ks,
+            "autotune_s": t_tune, "autotune_K": ks, "bf16_sound_where_served": bf16_sound,
             "wall_clock_note": "host-timed with synchronisation (one counter read per level)"}
 
 

@@ -228,10 +228,15 @@ typedef struct {
  * hands each CTA groups of nodes of one network, heaviest networks first),
  * and one segmented compaction serves every segment. counts: device
  * int64[n_segs][SRA_CNT_N], zeroed by the caller (or holding earlier
- * chunks' totals, which are appended after). FP32 only: every opts[k] has
- * precision SRA_PREC_FP32 and recheck 0, else SRA_EUNSUPPORTED. Segments
- * must not overlap in frontier_out or leaves_out. Uses stream-ordered scratch
- * of about 2 KB per segment plus one byte per node. Asynchronous. */
+ * chunks' totals, which are appended after). Precision FP32 (the SIMT
+ * launches above) or, for networks with the tensor-core path (3 -> H x L -> 1
+ * ReLU, H = 128 or 256) and affine-truncate K = 64, SRA_PREC_BF16 /
+ * SRA_PREC_BF16_SOUND: each such segment runs one tensor-core launch beside
+ * the SIMT launches (check sra_sync_status on its network for a timed-out
+ * wait). recheck and converge must be 0; FP64 is not batched; otherwise
+ * SRA_EUNSUPPORTED. Segments must not overlap in frontier_out or leaves_out.
+ * Uses stream-ordered scratch of about 2 KB per segment plus one byte per
+ * node. Asynchronous. */
 sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_opts *opts,
                                         int32_t n_nets, const float *root_lo, const float *root_hi,
                                         const sra_node *frontier_in, const sra_batch_seg *segs,

@@ -973,8 +973,15 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     for (int k = 0; k < n_nets; ++k) {
         if ((r = check_net(nets[k]))) return r;
         if ((r = check_opts(&opts[k]))) return r;
-        if (opts[k].precision != SRA_PREC_FP32 || opts[k].recheck || opts[k].converge)
-            return fail(SRA_EUNSUPPORTED, "batched rounds run in FP32 without re-check or convergence test (opts[%d])", k);
+        const int pr = opts[k].precision;
+        if (pr == SRA_PREC_FP64 || opts[k].recheck || opts[k].converge)
+            return fail(SRA_EUNSUPPORTED,
+                        "batched rounds run in FP32 or BF16 without re-check or convergence test (opts[%d])", k);
+        if ((pr == SRA_PREC_BF16 || pr == SRA_PREC_BF16_SOUND) &&
+            (!nets[k]->tc_ok || opts[k].arith != SRA_ARITH_AFFINE_TRUNCATE || opts[k].K != 64))
+            return fail(SRA_EUNSUPPORTED,
+                        "batched BF16 segments need a network with the tensor-core path and affine-truncate K = 64 "
+                        "(opts[%d])", k);
     }
     cudaStream_t st = as_stream(stream);
     unsigned char n3[kMaxKdLevels][3], axis[kMaxKdLevels];
@@ -983,6 +990,7 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     std::vector<BatchSplitSeg> ss(n_segs);
     std::vector<int> kmaxes(n_segs);
     std::vector<double> chunk_cost(n_segs);
+    std::vector<char> on_tc(n_segs, 0);  // bounded on the tensor cores (BF16 / BF16-sound)
     long long cls_n = 0, nblk = 0;
     for (int s = 0; s < n_segs; ++s) {
         const sra_batch_seg &g = segs[s];
@@ -997,14 +1005,18 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
             return fail(SRA_EINVAL, "segment %d: negative or oversized range", s);
         if ((g.n > 0 && !in) || (g.cap_out > 0 && !out) || (g.cap_leaves > 0 && !leaves))
             return fail(SRA_EINVAL, "segment %d: null buffer", s);
-        int kmax = 0;
-        if ((r = kmax_for(n, o, 3, &kmax))) return r;
-        RangeCfg cfg;
-        if ((r = make_cfg(n, o, kmax, 4, o->block_threads > 0 ? o->block_threads : 256, &cfg))) return r;
-        cfg.threads = cfg.NB * cfg.H;
-        kmaxes[s] = kmax;
         BatchSegDev &D = ds[s];
         memset(&D, 0, sizeof D);
+        on_tc[s] = o->precision == SRA_PREC_BF16 || o->precision == SRA_PREC_BF16_SOUND;
+        int kmax = 0;
+        RangeCfg cfg;
+        memset(&cfg, 0, sizeof cfg);
+        if (!on_tc[s]) {
+            if ((r = kmax_for(n, o, 3, &kmax))) return r;
+            if ((r = make_cfg(n, o, kmax, 4, o->block_threads > 0 ? o->block_threads : 256, &cfg))) return r;
+            cfg.threads = cfg.NB * cfg.H;
+        }
+        kmaxes[s] = kmax;
         D.net = n->dev;
         D.cfg = cfg;
         D.src.kind = SRC_NODES;
@@ -1018,7 +1030,7 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
         }
         double per_box = 0;
         for (int l = 0; l < n->L; ++l) per_box += (double)n->widths[l] * n->widths[l + 1] * (kmax + 2);
-        chunk_cost[s] = per_box * cfg.NB;
+        chunk_cost[s] = per_box * (cfg.NB > 0 ? cfg.NB : 1);
         BatchSplitSeg &S = ss[s];
         memset(&S, 0, sizeof S);
         S.first = g.first;
@@ -1037,7 +1049,10 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     // launches: one per (noise-column bound, CTA shape), segments heaviest
     // chunk first; the launches run concurrently on pooled streams
     std::vector<std::pair<int, int>> kinds;
+    std::vector<int> tc_segs;  // one tensor-core launch each, beside the SIMT launches
     for (int s = 0; s < n_segs; ++s) {
+        if (segs[s].n > 0 && on_tc[s]) tc_segs.push_back(s);
+        if (on_tc[s]) continue;
         const std::pair<int, int> key(kmaxes[s], ds[s].cfg.threads);
         if (segs[s].n > 0 && std::find(kinds.begin(), kinds.end(), key) == kinds.end()) kinds.push_back(key);
     }
@@ -1049,7 +1064,7 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
         Launch L = {km, (int)order.size(), 0, 0, 0, 0, 0.0};
         std::vector<int> mine;
         for (int s = 0; s < n_segs; ++s)
-            if (segs[s].n > 0 && kmaxes[s] == km && ds[s].cfg.threads == kk.second) mine.push_back(s);
+            if (segs[s].n > 0 && !on_tc[s] && kmaxes[s] == km && ds[s].cfg.threads == kk.second) mine.push_back(s);
         std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) { return chunk_cost[a] > chunk_cost[b]; });
         for (int s : mine) {
             ds[s].chunk0 = L.chunks;
@@ -1086,7 +1101,23 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     for (size_t k = 0; k < lorder.size(); ++k) lorder[k] = k;
     std::stable_sort(lorder.begin(), lorder.end(),
                      [&](size_t a, size_t b) { return launches[a].work > launches[b].work; });
-    if ((r = fork_join(st, (int)launches.size(), [&](int q, cudaStream_t ls) -> sra_status {
+    const int n_simt = (int)launches.size();
+    if ((r = fork_join(st, n_simt + (int)tc_segs.size(), [&](int q, cudaStream_t ls) -> sra_status {
+             if (q >= n_simt) {  // a tensor-core segment: its nodes, its classes
+                 const int s = tc_segs[q - n_simt];
+                 const sra_net *n = nets[segs[s].net];
+                 BoundOut bo;
+                 memset(&bo, 0, sizeof bo);
+                 bo.cls = ds[s].out.cls;
+                 const long long tiles = (segs[s].n + 1) / 2;
+                 long long grid = num_sms();
+                 if (grid > tiles) grid = tiles;
+                 cudaError_t e = launch_tc_bound(n->tc_H, opts[segs[s].net].precision == SRA_PREC_BF16_SOUND, n->tcp,
+                                                 ds[s].src, bo, (int)grid, ls);
+                 if (e != cudaSuccess)
+                     return fail(SRA_ECUDA, "batched tensor-core bound launch: %s", cudaGetErrorString(e));
+                 return SRA_OK;
+             }
              const size_t k = lorder[q];
              const Launch &L = launches[k];
              cudaError_t e = launch_multi_bound_f32(L.kmax, dsd, ordd + L.off, L.cnt, L.chunks, next + k,

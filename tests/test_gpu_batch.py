@@ -122,16 +122,46 @@ def test_batch_appends_to_counts(sra):
         nets[0].close()
 
 
-def test_batch_rejects_bf16(sra):
-    mlp = wl.make_mlp([128] * 3, "relu", seed=1)
-    net = sra.Net(mlp)
+def test_batch_bf16_segments_equal_lone_rounds(sra):
+    """Segments in BF16-sound and plain BF16 (their networks have the
+    tensor-core path) run beside FP32 segments in one batched round; each
+    equals a lone round with the same options."""
+    specs = [
+        (wl.make_mlp([128] * 4, "relu", seed=31), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 1001, 6),
+        (wl.net_small_relu(), dict(arith="truncate", K=16), 3, 500, 7),
+        (wl.make_mlp([256] * 3, "relu", seed=32), dict(arith="truncate", K=64, precision="bf16"), 5, 777, 5),
+        (wl.make_mlp([256] * 5, "relu", seed=33), dict(arith="truncate", K=64, precision="bf16_sound"), 3, 3, 9),
+        (wl.make_mlp([64] * 4, "elu", seed=34), dict(arith="fixed"), 4, 900, 8),
+    ]
+    nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
+    try:
+        counts = sra.classify_and_split_batch(nets, opts, frontier, segs, out, leaves)
+        for n in nets:
+            sra.sync_status(n)
+        check_against_lone(sra, nets, opts, frontier, segs, out, leaves, counts)
+        cnt = counts.cpu().numpy()
+        assert cnt[2][1] > 0  # the BF16 segment at its max level emitted leaves
+    finally:
+        for n in nets:
+            n.close()
+
+
+def test_batch_rejects_unserved_bf16(sra):
+    """BF16 segments need the tensor-core path (ReLU, width 128 or 256) and
+    affine-truncate K = 64; FP64 and re-checks are not batched."""
+    net = sra.Net(wl.make_mlp([64] * 3, "relu", seed=1))  # width 64: no tensor-core path
+    net2 = sra.Net(wl.make_mlp([128] * 3, "relu", seed=1))
     try:
         fr = sra.nodes_to_tensor(wl.random_nodes(10, 3))
         out = torch.empty((80, 4), dtype=torch.int16, device="cuda")
-        with pytest.raises(sra.SraError) as e:
-            sra.classify_and_split_batch([net], [sra.make_opts(arith="truncate", K=64, precision="bf16_sound")],
-                                         fr, [dict(net=0, max_level=5, n=10, cap_out=80, cap_leaves=0)],
-                                         out, out)
-        assert e.value.code == sra.EUNSUPPORTED
+        seg = [dict(net=0, max_level=5, n=10, cap_out=80, cap_leaves=0)]
+        for n, o in ((net, sra.make_opts(arith="truncate", K=64, precision="bf16_sound")),
+                     (net2, sra.make_opts(arith="truncate", K=32, precision="bf16_sound")),
+                     (net2, sra.make_opts(arith="truncate", K=64, precision="fp64")),
+                     (net2, sra.make_opts(arith="truncate", K=64, precision="bf16", recheck=True))):
+            with pytest.raises(sra.SraError) as e:
+                sra.classify_and_split_batch([n], [o], fr, seg, out, out)
+            assert e.value.code == sra.EUNSUPPORTED
     finally:
         net.close()
+        net2.close()
