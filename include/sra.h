@@ -249,10 +249,12 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * when opts->max_iters ran out; and iters[i] (device int32[n], may be NULL):
  * loop iterations taken. One persistent launch refills finished ray slots.
  * opts->precision: SRA_PREC_FP32 (and SRA_PREC_FP64) runs every step on the
- * SIMT cores in FP32 (FP64), any arithmetic; SRA_PREC_BF16 runs the hidden
- * H -> H layers on the tensor cores (tcgen05) with the weights and every
- * operand split into BF16 hi/lo pairs and FP32 accumulation (about 16
- * significant bits per product; plain arithmetic, no rounding radius). BF16
+ * SIMT cores in FP32 (FP64), any arithmetic; SRA_PREC_BF16 runs every layer
+ * but the output one on the tensor cores (tcgen05) with the weights and the
+ * center, point and noise operands split into BF16 hi/lo pairs and FP32
+ * accumulation (about 16 significant bits per product), and |W| x_inf from
+ * |W| and x_inf rounded up to BF16 (an upper bound of that term); plain
+ * arithmetic otherwise, no rounding radius. BF16
  * needs affine-fixed arithmetic and a network whose hidden layers all have
  * one width H in {128, 256, 512}, with 1 to 8 H -> H layers and an input
  * width (after the encoding) of at most 64; otherwise SRA_EUNSUPPORTED. A

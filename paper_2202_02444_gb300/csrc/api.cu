@@ -409,7 +409,7 @@ void prepare_tc(sra_net *n, const float *params) {
 // Prepare the tensor-core ray kernel if the network has its shape: every
 // hidden width H in {128, 256, 512}, 1 <= L-2 <= 8 hidden H -> H layers, an
 // input width (after the positional encoding) of at most 64, scalar output.
-// Each layer becomes four BF16 matrices (W_b, W_r, |W_b|, sign(W_b) W_r);
+// Each layer becomes three BF16 matrices (W_b, W_r, and |W| rounded up);
 // layer 0's K is padded to 64 with zero columns.
 void prepare_tc_rays(sra_net *n, const float *params) {
     const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
@@ -419,37 +419,45 @@ void prepare_tc_rays(sra_net *n, const float *params) {
         if (n->widths[l] != H) return;
     const int nh = L - 2;
     const size_t per_h = (size_t)H * H * 2, per_0 = (size_t)H * 64 * 2;
-    const size_t bytes = 4 * per_0 + 4 * nh * per_h + 256;
+    const size_t bytes = 3 * per_0 + 3 * nh * per_h + 256;
     if (cudaMalloc(&n->tcr_buf, bytes) != cudaSuccess) { n->tcr_buf = nullptr; cudaGetLastError(); return; }
     TcRayParams &t = n->tcrp;
     memset(&t, 0, sizeof t);
-    // four matrices of one layer, from W [H][K_in] zero-padded to [H][K]
+    // smallest BF16 >= x for x >= 0 (the next bit pattern up is the next
+    // larger value of a non-negative BF16)
+    auto bf16_up = [](float x) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        if (__bfloat162float(h) < x) {
+            uint16_t b;
+            memcpy(&b, &h, 2);
+            ++b;
+            memcpy(&h, &b, 2);
+        }
+        return h;
+    };
+    // three matrices of one layer, from W [H][K_in] zero-padded to [H][K]
     auto upload = [&](const float *W, int k_in, int K, char *dst, TcLayerMaps &maps) -> bool {
         const size_t per = (size_t)H * K;
-        std::vector<__nv_bfloat16> m(4 * per);
+        std::vector<__nv_bfloat16> m(3 * per);
         for (int r = 0; r < H; ++r)
             for (int k = 0; k < K; ++k) {
                 const float w = k < k_in ? W[(size_t)r * k_in + k] : 0.f;
                 const __nv_bfloat16 h = __float2bfloat16_rn(w);
-                const float hf = __bfloat162float(h);
-                const __nv_bfloat16 lo = __float2bfloat16_rn(w - hf);
                 const size_t e = (size_t)r * K + k;
                 m[e] = h;
-                m[per + e] = lo;
-                m[2 * per + e] = __float2bfloat16_rn(std::fabs(hf));
-                m[3 * per + e] = __float2bfloat16_rn(hf < 0.f ? -__bfloat162float(lo) : __bfloat162float(lo));
+                m[per + e] = __float2bfloat16_rn(w - __bfloat162float(h));
+                m[2 * per + e] = bf16_up(std::fabs(w));
             }
         const size_t b = per * 2;
-        return cudaMemcpy(dst, m.data(), 4 * b, cudaMemcpyHostToDevice) == cudaSuccess &&
+        return cudaMemcpy(dst, m.data(), 3 * b, cudaMemcpyHostToDevice) == cudaSuccess &&
                make_bf16_tile_map(&maps.wb, dst, H, K, 128, 64) == 0 &&
                make_bf16_tile_map(&maps.wr, dst + b, H, K, 128, 64) == 0 &&
-               make_bf16_tile_map(&maps.wa, dst + 2 * b, H, K, 128, 64) == 0 &&
-               make_bf16_tile_map(&maps.ws, dst + 3 * b, H, K, 128, 64) == 0;
+               make_bf16_tile_map(&maps.wa, dst + 2 * b, H, K, 128, 64) == 0;
     };
     bool ok = upload(params, n->din, 64, (char *)n->tcr_buf, t.first);
     size_t off = (size_t)n->din * H + H;  // layer 1 starts after W0, b0
     for (int l = 1; ok && l <= nh; ++l) {
-        ok = upload(params + off, H, H, (char *)n->tcr_buf + 4 * per_0 + 4 * (l - 1) * per_h, t.hidden[l - 1]);
+        ok = upload(params + off, H, H, (char *)n->tcr_buf + 3 * per_0 + 3 * (l - 1) * per_h, t.hidden[l - 1]);
         off += (size_t)H * H + H;
     }
     if (!ok) {
@@ -465,7 +473,7 @@ void prepare_tc_rays(sra_net *n, const float *params) {
     t.L = L;
     t.din = n->din;
     t.pe = n->pe;
-    t.status = (int *)((char *)n->tcr_buf + 4 * per_0 + 4 * nh * per_h);
+    t.status = (int *)((char *)n->tcr_buf + 3 * per_0 + 3 * nh * per_h);
     cudaMemset(t.status, 0, sizeof(int));
     n->tcr_H = H;
     n->tcr_ok = true;

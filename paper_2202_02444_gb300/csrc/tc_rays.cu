@@ -9,17 +9,20 @@
 //
 // Linear layer l is two tensor-core products into TMEM (FP32 accumulation):
 //   D  = (W_b + W_r) [c_hi c_lo p_hi p_lo A_hi A_lo]     96 operand rows
-//   Dx = (|W_b| + sign(W_b) W_r) [x_hi x_lo]              32 operand rows
-// W = W_b + W_r is the BF16 hi/lo split of the FP32 weights (|W_b + W_r| =
-// |W_b| + sign(W_b) W_r, since |W_r| <= 2^-8 |W_b|), and every operand value
-// rides as a BF16 hi/lo pair, so each product keeps about 16 significant bits
-// before the FP32 sums. Layer 0 takes the encoded input rows (K padded to 64).
+//   Dx = |W|_ru x_ru                                      16 operand rows
+// W = W_b + W_r is the BF16 hi/lo split of the FP32 weights, and the center,
+// point and noise values ride as BF16 hi/lo pairs, so each of their products
+// keeps about 16 significant bits before the FP32 sums. The independent part
+// x_inf is non-negative and only ever multiplied by |W|: both ride rounded up
+// to BF16 (|W|_ru >= |W|, x_ru >= x_inf), so Dx bounds |W| x_inf from above
+// with one matrix and one operand row per ray. Layer 0 takes the encoded
+// input rows (K padded to 64).
 //
 // The weights stream from L2 by TMA as 16 KB tiles (128 rows x 64 K of one
 // matrix) through a ring that runs ahead across layers and march steps. One
 // thread issues the copies (it refills a stage once the MMAs that read it
 // have completed), another issues the MMAs (one tile = 4 MMAs of K = 16;
-// tiles in pairs, a D tile and a Dx tile, their MMAs alternating),
+// tiles in pairs of consecutive units, their MMAs alternating),
 // and the whole CTA then runs the epilogue: per neuron and ray, the range,
 // the activation rule (App. A) and the operand rows of the next layer. The
 // encoding, the output layer and the march state run on the SIMT cores in
@@ -38,13 +41,13 @@ namespace tcr {
 
 constexpr int NR = 16;      // ray slots per CTA
 constexpr int NCOL = 96;    // operand rows of D: 6 per ray
-constexpr int NXI = 32;     // operand rows of Dx: 2 per ray
+constexpr int NXI = 16;     // operand rows of Dx: 1 per ray
 constexpr int MAXDIN = 64;  // input width (3 + 6 * octaves) bound: layer 0 has one K slice
 constexpr int TILE = 128 * 128;
 constexpr int kSmemCap = 232448;
 constexpr uint32_t kSpin = 1u << 22;
 enum { C_HI = 0, C_LO = 16, P_HI = 32, P_LO = 48, A_HI = 64, A_LO = 80 };
-enum { X_HI = 0, X_LO = 16 };
+enum { X_RU = 0 };
 
 struct RaySlot {
     long long idx;
@@ -70,7 +73,7 @@ template <int H> struct RL {
     static constexpr int NSTG_FIT = (kSmemCap - 1024 - RING_OFF) / TILE;
     static constexpr int NSTG = NSTG_FIT >= 8 ? 8 : 4;  // 4 measured faster than 5 at H = 512
     static constexpr int ALLOC = RING_OFF + NSTG * TILE + 1024;
-    static constexpr int TCOLS = MT * 128;                       // TMEM: D (96) + Dx (32) per M-tile
+    static constexpr int TCOLS = MT * 128;                       // TMEM: D (96) + Dx (16) per M-tile
     static_assert(NSTG_FIT >= 4, "weight ring");
     static_assert(MT == 1 || MT == 2 || MT == 4, "M tiles");
     static_assert(2 * NSTG + 2 <= 32, "barrier slots");
@@ -100,7 +103,7 @@ __device__ __forceinline__ void write_rows(unsigned char *sm, int k, int r, floa
     put_pair(xb, C_HI + r, C_LO + r, kk, c);
     put_pair(xb, P_HI + r, P_LO + r, kk, p);
     put_pair(xb, A_HI + r, A_LO + r, kk, A);
-    put_pair(xs, X_HI + r, X_LO + r, kk, xi);
+    *(__nv_bfloat16 *)(xs + ptx::sw128_offset((uint32_t)(X_RU + r), kk)) = __float2bfloat16_ru(xi);  // xi >= 0
 }
 
 // Activation of one neuron for one ray: the affine rule (App. A) on the
@@ -117,13 +120,13 @@ __device__ __forceinline__ void activate(int act, int slope, float &c, float &A,
     p = act_eval<float>(act, p);
 }
 
-// A ring unit: one 128 x 64 tile (M tile m, K slice s) of one of the four
-// matrices of linear layer `layer`. Within a layer the units run K slice by
-// K slice, M tile by M tile, matrix by matrix in the order W_b, |W_b|, W_r,
-// sign W_r, so that consecutive units feed the two accumulators D and Dx: the
-// MMA thread takes them in pairs and alternates their MMAs, and neither
-// chain of dependent accumulations waits on itself back to back. Each
-// accumulator still receives W_b's products before W_r's.
+// A ring unit: one 128 x 64 tile (M tile m, K slice s) of one of the three
+// matrices of linear layer `layer` (0 W_b, 1 W_r: into D; 2 |W|_ru: into
+// Dx). Within a layer the units run K slice by K slice, M tile by M tile, in
+// the order W_b, |W|_ru, W_r, so that two consecutive units feed different
+// accumulators (D and Dx of one M tile, or D of two M tiles when there are
+// two or more): the MMA thread takes them in pairs and alternates their MMAs.
+// Each accumulator D still receives W_b's products before W_r's.
 struct Unit {
     int layer, s, m, which;
 };
@@ -132,8 +135,8 @@ template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
     using L = RL<H>;
     Unit r;
     r.layer = layer;
-    r.which = (u & 1) * 2 + ((u >> 1) & 1);  // 0 W_b, 2 |W_b|, 1 W_r, 3 sign W_r
-    const int ms = u >> 2;
+    const int ms = u / 3, w = u - 3 * ms;
+    r.which = w == 0 ? 0 : (w == 1 ? 2 : 1);
     r.m = ms & (L::MT - 1);
     r.s = ms / L::MT;
     return r;
@@ -141,7 +144,7 @@ template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
 
 template <int H> __device__ __forceinline__ int units_of(int layer) {
     using L = RL<H>;
-    return layer == 0 ? 4 * L::MT : 4 * L::MT * L::S;
+    return layer == 0 ? 3 * L::MT : 3 * L::MT * L::S;
 }
 
 // A position in the weight ring: its stage and the parity of that stage's
@@ -176,7 +179,7 @@ __device__ __forceinline__ bool ring_load(unsigned char *sm, uint64_t *bars, con
     if (!ptx::mbar_wait(&bars[L::NSTG + st], c.pos.ph ^ 1u, kSpin)) return false;
     const Unit u = unit_of<H>(c.layer, c.u);
     const TcLayerMaps &mp = u.layer == 0 ? p.first : p.hidden[u.layer - 1];
-    const CUtensorMap *map = u.which == 0 ? &mp.wb : (u.which == 1 ? &mp.wr : (u.which == 2 ? &mp.wa : &mp.ws));
+    const CUtensorMap *map = u.which == 0 ? &mp.wb : (u.which == 1 ? &mp.wr : &mp.wa);
     unsigned char *dst = sm + L::RING_OFF + st * TILE;
     ptx::mbar_arrive_expect_tx(&bars[st], TILE);
     ptx::tma_load_2d(dst, map, u.s * 64, u.m * 128, &bars[st]);
@@ -311,26 +314,25 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             } else if (issuer) {
                 bool ok = true;
                 const uint32_t iD = ptx::idesc_bf16(128, NCOL), iX = ptx::idesc_bf16(128, NXI);
-                // two units at a time (a D unit and a Dx unit): their MMAs
-                // alternate between the two accumulators
-                for (uint32_t k = 0; k < U && ok; k += 2) {
+                // two consecutive units at a time (they feed different
+                // accumulators): their MMAs alternate; an odd last unit alone
+                for (uint32_t k = 0; k < U && ok;) {
+                    const int nj = (U - k >= 2u) ? 2 : 1;
                     RingPos pos[2];
-                    pos[0] = ipos;
-                    advance<H>(ipos);
-                    pos[1] = ipos;
-                    advance<H>(ipos);
                     uint32_t d_col[2], idesc[2];
                     uint64_t a0[2], b0[2];
                     bool first[2];
-                    for (int j = 0; j < 2; ++j) {
+                    for (int j = 0; j < nj; ++j) {
+                        pos[j] = ipos;
+                        advance<H>(ipos);
                         if (!ptx::mbar_wait(&bars[pos[j].st], pos[j].ph, kSpin)) { ok = false; break; }
                         const Unit u = unit_of<H>(l, (int)k + j);
-                        const bool dx = u.which >= 2;
+                        const bool dx = u.which == 2;
                         const uint32_t b_addr = dx ? ptx::smem_u32(sm + L::XI_OFF + u.s * L::XI_SLICE)
                                                    : ptx::smem_u32(sm + L::XB_OFF + u.s * L::XB_SLICE);
                         d_col[j] = tmem + (uint32_t)(u.m * 128 + (dx ? NCOL : 0));
                         idesc[j] = dx ? iX : iD;
-                        first[j] = (u.which & 1) == 0 && u.s == 0;
+                        first[j] = u.which != 1 && u.s == 0;  // W_b into D, |W| into Dx: slice 0 starts them
                         a0[j] = ptx::desc_kmajor_sw128(ptx::smem_u32(sm + L::RING_OFF + pos[j].st * TILE));
                         b0[j] = ptx::desc_kmajor_sw128(b_addr);
                     }
@@ -338,13 +340,12 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                     ptx::tc_fence_after();
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks)
-#pragma unroll
-                        for (int j = 0; j < 2; ++j)
+                        for (int j = 0; j < nj; ++j)
                             ptx::mma_bf16(d_col[j], a0[j] + 2 * ks, b0[j] + 2 * ks, idesc[j],
                                           (first[j] && ks == 0) ? 0u : 1u);
-                    ptx::mma_commit(&bars[L::NSTG + pos[0].st]);
-                    ptx::mma_commit(&bars[L::NSTG + pos[1].st]);
-                    if (k + 2 == U) ptx::mma_commit(acc_bar);
+                    for (int j = 0; j < nj; ++j) ptx::mma_commit(&bars[L::NSTG + pos[j].st]);
+                    k += (uint32_t)nj;
+                    if (k == U) ptx::mma_commit(acc_bar);
                 }
                 *consumed += U;  // published once per layer for the exit drain
                 *issue_pos = ipos;
@@ -370,15 +371,14 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 ptx::tmem_ld8(tl + P_LO + r0, v + 24);
                 ptx::tmem_ld8(tl + A_HI + r0, v + 32);
                 ptx::tmem_ld8(tl + A_LO + r0, v + 40);
-                ptx::tmem_ld8(tl + NCOL + X_HI + r0, v + 48);
-                ptx::tmem_ld8(tl + NCOL + X_LO + r0, v + 56);
+                ptx::tmem_ld8(tl + NCOL + X_RU + r0, v + 48);
                 ptx::tmem_wait_ld();
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     float c = (v[r] + v[8 + r]) + bias;
                     float pp = (v[16 + r] + v[24 + r]) + bias;
                     float A = v[32 + r] + v[40 + r];
-                    float xi = v[48 + r] + v[56 + r];
+                    float xi = v[48 + r];
                     activate(act, p.slope, c, A, xi, pp);
                     write_rows<H>(sm, i, r0 + r, c, A, xi, pp);
                 }
@@ -397,7 +397,10 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 const float w = wout[j];
                 if (kind == 0) acc = fmaf(w, get_pair(xb, C_HI + r, C_LO + r, kk), acc);
                 else if (kind == 1) acc = fmaf(w, get_pair(xb, A_HI + r, A_LO + r, kk), acc);
-                else if (kind == 2) acc = fmaf(fabsf(w), get_pair(xs, X_HI + r, X_LO + r, kk), acc);
+                else if (kind == 2)
+                    acc = fmaf(fabsf(w),
+                               __bfloat162float(*(const __nv_bfloat16 *)(xs + ptx::sw128_offset((uint32_t)(X_RU + r), kk))),
+                               acc);
                 else acc = fmaf(w, get_pair(xb, P_HI + r, P_LO + r, kk), acc);
             }
             outp[q * L::NPART + part] = acc;

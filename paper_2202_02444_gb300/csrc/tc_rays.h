@@ -10,11 +10,11 @@ namespace sra {
 
 constexpr int kMaxRayTc = 8;  // hidden H -> H layers served by the tensor cores
 
-// One linear layer as four BF16 matrices, row-major [H][K] (K-major tiles):
-// W_b = bf16(W), W_r = bf16(W - W_b), |W_b|, and sign(W_b) W_r, so that
-// W_b + W_r ~ W and |W_b| + sign(W_b) W_r = |W_b + W_r| (|W_r| <= 2^-8 |W_b|).
+// One linear layer as three BF16 matrices, row-major [H][K] (K-major tiles):
+// W_b = bf16(W), W_r = bf16(W - W_b) (W_b + W_r ~ W), and |W| rounded up to
+// BF16 (an upper bound of |W| for the x_inf product).
 struct TcLayerMaps {
-    CUtensorMap wb, wr, wa, ws;
+    CUtensorMap wb, wr, wa;
 };
 
 struct TcRayParams {
