@@ -12,7 +12,8 @@
 // pre-activations, for one, a c + b is much smaller than its terms). Per
 // linear layer (App. A Table "affine_update_rules"):
 //   * full_gemm_kernel: Y = W X for every box of the chunk (one batched GEMM,
-//     64 x 64 output tiles, K staged through shared memory in slices of 16);
+//     128 x 128 output tiles, 8 x 8 per thread, K staged through two
+//     shared-memory buffers in slices of 8);
 //   * full_center_kernel: the center W c + b in FP64 from the FP64 copy of
 //     the weights;
 //   * full_act_kernel, one warp per row: the range (Eq. def_range: the sum of
@@ -37,8 +38,9 @@ template <typename T> const T *b_host(const LayerDev &L);
 template <> const float *b_host<float>(const LayerDev &L) { return L.b; }
 template <> const double *b_host<double>(const LayerDev &L) { return L.b64; }
 
-constexpr int GT = 64;   // GEMM output tile (rows and columns)
-constexpr int GK = 16;   // GEMM K slice
+constexpr int GM = 128;  // GEMM output tile: rows
+constexpr int GN = 128;  // GEMM output tile: columns
+constexpr int GK = 8;    // GEMM K slice
 constexpr int ACT_ROWS = 8;  // rows per CTA of the activation kernel (one warp each)
 
 __device__ __forceinline__ long long boxes_in_chunk(const BoxSrc &src, long long c0, long long nb) {
@@ -96,51 +98,92 @@ __global__ void full_init_kernel(NetDev net, BoxSrc src, T *X, double *cen, int 
     }
 }
 
+// Four consecutive elements from global memory: one 16-byte load when the
+// whole run lies inside [0, lim) and `vec` (16-byte alignment of the run),
+// else element by element with zero fill.
+template <typename T>
+__device__ __forceinline__ void gload4(const T *p, long long i, long long lim, bool vec, T *v) {
+    if (vec && i + 3 < lim) {
+        load4(p + i, v);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (i + q < lim) ? p[i + q] : T(0);
+    }
+}
+
 // Y[b] (M x N) = W (M x K) X[b] (K x N) for the boxes of the chunk; W is
-// given transposed, Wt [K][M]. 256 threads, 4 x 4 outputs each.
+// given transposed, Wt [K][M]. CTA tile GM x GN, K slices of GK staged
+// through two shared-memory buffers (the next slice's global loads are in
+// flight while the current one is multiplied); 256 threads, each 8 x 8
+// outputs (rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, columns likewise with
+// tx). Every output is summed over k in ascending order.
 template <typename T>
 __global__ void __launch_bounds__(256) full_gemm_kernel(const T *__restrict__ Wt, int M, int K,
                                                          const T *__restrict__ X, T *__restrict__ Y, int N, int LD,
                                                          long long rs, BoxSrc src, long long c0, long long nb) {
-    __shared__ __align__(16) T As[GK][GT];  // As[k][m] = W[m0 + m][k0 + k]
-    __shared__ __align__(16) T Bs[GK][GT];  // Bs[k][n] = X[k0 + k][n0 + n]
+    __shared__ __align__(16) T As[2][GK][GM];  // As[.][k][m] = W[m0 + m][k0 + k]
+    __shared__ __align__(16) T Bs[2][GK][GN];  // Bs[.][k][n] = X[k0 + k][n0 + n]
     const long long b = blockIdx.z;
     if (b >= boxes_in_chunk(src, c0, nb)) return;
     const T *Xb = X + b * rs;
     T *Yb = Y + b * rs;
-    const int m0 = blockIdx.y * GT, n0 = blockIdx.x * GT;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    T acc[4][4];
+    const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    // this thread's share of a slice: row lk of the slice, four elements at lc
+    const int lk = tid >> 5, lc = (tid & 31) * 4;
+    const bool avec = (M & 3) == 0, bvec = (LD & 3) == 0;
+    T ra[4], rb[4];
+    auto fetch = [&](int k0) {
+        const int k = k0 + lk;
+        if (k < K) {
+            gload4(Wt + (long long)k * M, (long long)(m0 + lc), (long long)M, avec, ra);
+            gload4(Xb + (long long)k * LD, (long long)(n0 + lc), (long long)N, bvec, rb);
+        } else {
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = T(0);
-    for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int e = threadIdx.x; e < GK * GT; e += 256) {
-            const int kk = e / GT, mm = e - kk * GT;
-            As[kk][mm] = (k0 + kk < K && m0 + mm < M) ? __ldg(Wt + (long long)(k0 + kk) * M + m0 + mm) : T(0);
-            Bs[kk][mm] = (k0 + kk < K && n0 + mm < N) ? Xb[(long long)(k0 + kk) * LD + n0 + mm] : T(0);
+            for (int q = 0; q < 4; ++q) ra[q] = rb[q] = T(0);
         }
-        __syncthreads();
+    };
+    auto stash = [&](int buf) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            As[buf][lk][lc + q] = ra[q];
+            Bs[buf][lk][lc + q] = rb[q];
+        }
+    };
+    T acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] = T(0);
+    const int nt = (K + GK - 1) / GK;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int t = 0; t < nt; ++t) {
+        const int cur = t & 1;
+        if (t + 1 < nt) fetch((t + 1) * GK);
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            T a[4], v[4];
-            load4(&As[kk][ty * 4], a);
-            load4(&Bs[kk][tx * 4], v);
+            T a[8], v[8];
+            load4(&As[cur][kk][ty * 4], a);
+            load4(&As[cur][kk][64 + ty * 4], a + 4);
+            load4(&Bs[cur][kk][tx * 4], v);
+            load4(&Bs[cur][kk][64 + tx * 4], v + 4);
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < 8; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = fma(a[r], v[q], acc[r][q]);
+                for (int q = 0; q < 8; ++q) acc[r][q] = fma(a[r], v[q], acc[r][q]);
         }
+        if (t + 1 < nt) stash(cur ^ 1);
         __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int m = m0 + ty * 4 + r;
+    for (int r = 0; r < 8; ++r) {
+        const int m = m0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + r - 4);
         if (m >= M) continue;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int n = n0 + tx * 4 + q;
+        for (int q = 0; q < 8; ++q) {
+            const int n = n0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
             if (n < N) Yb[(long long)m * LD + n] = acc[r][q];
         }
     }
@@ -241,7 +284,7 @@ cudaError_t full_hbm_t(const NetDev &net, const FullHbmCfg &fc, const BoxSrc &sr
         for (int l = 0; l + 1 < net.L; ++l) {
             const LayerDev &Ld = net.layer[l];
             const int M = Ld.out, K = Ld.in, N = 1 + S;
-            const dim3 gg((unsigned)((N + GT - 1) / GT), (unsigned)((M + GT - 1) / GT), (unsigned)nb);
+            const dim3 gg((unsigned)((N + GN - 1) / GN), (unsigned)((M + GM - 1) / GM), (unsigned)nb);
             full_gemm_kernel<T><<<gg, 256, 0, st>>>(Wt_host<T>(Ld), M, K, buf[cur], buf[cur ^ 1], N, fc.LD, rs, src,
                                                    c0, nb);
             full_center_kernel<<<dim3((unsigned)((M + 127) / 128), (unsigned)nb), 128, 0, st>>>(
