@@ -117,7 +117,7 @@ def parse_args():
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16"],
+                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16", "full_fp32"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
     ap.add_argument("--serve-rates", default="2,4,8,16", help="request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
@@ -550,7 +550,8 @@ def run_reference(args):
 def kernel_case(args):
     """The dominant kernel alone, for profilers: two sra_bound_boxes calls on
     --batch boxes (half-widths log-uniform in [1/1024, 1/64]) of the
-    3-[256]x8-1 ReLU net, affine-truncate K=64, in the given precision."""
+    3-[256]x8-1 ReLU net, affine-truncate K=64 in the given precision, or
+    affine-full in FP32 (full_fp32)."""
     import torch
     from paper_2202_02444_gb300 import sra
     if args.kernel_case in ("rays", "rays_bf16"):  # central camera rays, 300-iteration cap
@@ -570,7 +571,10 @@ def kernel_case(args):
     net = sra.Net(wl.net_relu256x8())
     c, h = wl.make_boxes(args.batch, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
     C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
-    o = sra.make_opts(arith="truncate", K=64, precision=args.kernel_case)
+    if args.kernel_case == "full_fp32":  # affine-full, the noise matrix in device memory
+        o = sra.make_opts(arith="full")
+    else:
+        o = sra.make_opts(arith="truncate", K=64, precision=args.kernel_case)
     for _ in range(2):
         sra.bound_boxes(net, C_, H_, opts=o)
     torch.cuda.synchronize()
