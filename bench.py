@@ -193,10 +193,10 @@ class ClockSampler:
 
 def tc_box_net(m):
     """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU
-    network with one hidden width H in {128, 256} and at most 12 hidden
+    or ELU network with one hidden width H in {128, 256} and at most 12 hidden
     tensor-core layers, no positional encoding."""
-    return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and all(a == 1 for a in m.acts)
-            and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
+    return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and len(set(m.acts)) == 1
+            and m.acts[0] in (1, 2) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
 
 
 def serving_nets():
@@ -225,8 +225,7 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
         return all(w == H for w in m.widths[1:-1]) and 1 <= m.n_layers - 2 <= 8
 
     ray_tc = [any(uniform(m, H) for H in (128, 256, 512)) and m.widths[0] <= 64 for m in mlps]
-    box_tc = [any(uniform(m, H) for H in (128, 256)) and all(a == 1 for a in m.acts) and
-              m.pe_octaves == 0 and m.n_layers - 2 <= 12 for m in mlps]
+    box_tc = [tc_box_net(m) for m in mlps]
     o_all, d_all = wl.camera_rays(64, 64)
     ro, rd = torch.from_numpy(o_all).to(dev), torch.from_numpy(d_all).to(dev)
     out = {"workload": "16 resident nets (12 of the uneven generator, seeds 1000..1011, + 4 ELU "

@@ -290,10 +290,11 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
                               long long count, unsigned long long *recheck_counter,
                               cudaStream_t st) {
     const bool bf16 = o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16;
-    if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || o->K != 64))
+    if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || o->K != 64 ||
+                 o->slope != SRA_SLOPE_CHEBYSHEV))
         return fail(SRA_EUNSUPPORTED,
-                    "BF16 tensor-core bounds need a 3 -> H x L -> 1 ReLU network (H = 128 or 256, at most %d hidden "
-                    "tensor-core layers) with affine-truncate K = 64",
+                    "BF16 tensor-core bounds need a 3 -> H x L -> 1 ReLU or ELU network (H = 128 or 256, at most %d "
+                    "hidden tensor-core layers) with affine-truncate K = 64 and the Chebyshev slope",
                     kMaxTcLayers);
     const bool fp64 = o->precision == SRA_PREC_FP64;
     const bool recheck = o->recheck && !fp64;
@@ -349,14 +350,17 @@ sra_status check_net(const sra_net *n) {
 }
 
 // Prepare the tensor-core path if the network has its shape: 3 inputs,
-// L-1 >= 2 hidden ReLU layers of one width H in {128, 256}, scalar output.
+// L-1 >= 2 hidden layers of one width H in {128, 256}, all ReLU or all ELU,
+// scalar output.
 void prepare_tc(sra_net *n, const float *params) {
     const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
     if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256)) return;
     for (int l = 1; l < L; ++l)
         if (n->widths[l] != H) return;
+    const int act = n->acts[0];
+    if (act != SRA_ACT_RELU && act != SRA_ACT_ELU) return;
     for (int l = 0; l + 1 < L; ++l)
-        if (n->acts[l] != SRA_ACT_RELU) return;
+        if (n->acts[l] != act) return;
     const int nh = L - 2;
     const size_t per = (size_t)H * H * 2;
     const size_t bytes = 2 * nh * per + 256;
@@ -388,6 +392,7 @@ void prepare_tc(sra_net *n, const float *params) {
     t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
     t.bout = params[off + H];         // the output layer's bias follows its H weights
     t.L = L;
+    t.act = act;
     t.status = (int *)((char *)n->tc_buf + 2 * nh * per);
     cudaMemset(t.status, 0, sizeof(int));
     // rounding constants (u = 2^-24, u_b = 2^-8); accumulation model: each
@@ -986,7 +991,8 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
             return fail(SRA_EUNSUPPORTED,
                         "batched rounds run in FP32 or BF16 without re-check or convergence test (opts[%d])", k);
         if ((pr == SRA_PREC_BF16 || pr == SRA_PREC_BF16_SOUND) &&
-            (!nets[k]->tc_ok || opts[k].arith != SRA_ARITH_AFFINE_TRUNCATE || opts[k].K != 64))
+            (!nets[k]->tc_ok || opts[k].arith != SRA_ARITH_AFFINE_TRUNCATE || opts[k].K != 64 ||
+             opts[k].slope != SRA_SLOPE_CHEBYSHEV))
             return fail(SRA_EUNSUPPORTED,
                         "batched BF16 segments need a network with the tensor-core path and affine-truncate K = 64 "
                         "(opts[%d])", k);

@@ -1,6 +1,6 @@
 // BF16-sound RangeBound on the tensor cores (tcgen05 + TMEM + TMA).
 //
-// Network shape served: 3 -> H -> ... -> H -> 1 ReLU MLP (H = 128 or 256),
+// Network shape served: 3 -> H -> ... -> H -> 1 ReLU or ELU MLP (H = 128 or 256),
 // affine-truncate with K = 64 kept noise symbols (Sec. 3.3), the dense layers
 // of App. A Table "affine_update_rules" on tensor cores. One persistent CTA per
 // SM runs the whole network for a tile of NB = 2 boxes with 2H threads: thread
@@ -19,7 +19,7 @@
 //   * x_inf' >= |W| v is accumulated by the SIMT threads from the resident
 //     W_b slice with round-up FMAs (|W| <= |W_b| / (1 - u_b));
 //   * epilogue, one thread per neuron (tcgen05.ld of its TMEM row): outward
-//     rounded range, the ReLU rule, truncation to the 64 largest columns, and
+//     rounded range, the ReLU or ELU rule, truncation to the 64 largest columns, and
 //     the a-priori rounding radius of every FP operation folded into x_inf.
 // The first layer (3 inputs) and the output layer (1 output) run on the SIMT
 // cores with directed rounding. Every bounded wait that runs out writes a
@@ -145,6 +145,79 @@ __device__ __forceinline__ void relu_rule(float sa, float c, float xinf, float u
         xi = ru_fma(fabsf(c2), 1.1920929e-07f, xi);  // one rounding: <= 2^-23 |c2|
         xi = ru_fma(__fmul_ru(al, sa), u_b2u, xi);
     }
+}
+
+// ELU(x) = x for x >= 0, else e^x - 1, bounded from above and below in FP32.
+// expm1f is within 1 ulp of e^x - 1 (CUDA's documented maximum error), i.e.
+// within 2^-23 of its result's magnitude; the bounds pad by 2^-22 of it plus
+// the smallest normal float.
+__device__ __forceinline__ float elu_pad(float e) { return ru_fma(fabsf(e), 2.3841858e-07f, 1.17549435e-38f); }
+__device__ __forceinline__ float elu_up(float x) {
+    if (x >= 0.f) return x;
+    const float e = expm1f(x);
+    return ru_add(e, elu_pad(e));
+}
+__device__ __forceinline__ float elu_dn(float x) {
+    if (x >= 0.f) return x;
+    const float e = expm1f(x);
+    return rd_add(e, -elu_pad(e));
+}
+
+// The ELU rule of App. A Table "affine_nonlinearities" (reading R2) for one
+// neuron, with the outputs of relu_rule. The slope is the FP32 Chebyshev
+// (secant) slope; in the sound form any slope in [0, 1] is valid because the
+// extremes of g(x) = ELU(x) - al x on the outward-rounded [lo, hi] are
+// bounded directly: g is convex, so its maximum sits at an end (each end
+// evaluated rounded up), and at any point x0 (here clamp(ln al, lo, hi)) the
+// tangent gives min g >= g(x0) - |g'(x0)| max(x0 - lo, hi - x0), every term
+// rounded outward (expf within 2 ulp, padded by 2^-21), and min g >= -1 - al
+// hi. Then
+// be = (r_u + r_l) / 2 and ga = max(r_u - be, be - r_l), rounded up.
+template <bool SOUND>
+__device__ __forceinline__ void elu_rule(float sa, float c, float xinf, float u_b2u, float &al, float &ga, float &c2,
+                                         float &xi) {
+    const float rad = ru_add(sa, xinf);
+    const float lo = rd_add(c, -rad), hi = ru_add(c, rad);
+    float be;
+    if (lo >= 0.f) {
+        al = 1.f; be = 0.f; ga = 0.f;
+    } else if (!SOUND) {
+        linearize<float>(SRA_ACT_ELU, SRA_SLOPE_CHEBYSHEV, lo, hi, al, be, ga);
+    } else {
+        float b0, g0;
+        linearize<float>(SRA_ACT_ELU, SRA_SLOPE_CHEBYSHEV, lo, hi, al, b0, g0);
+        al = fminf(fmaxf(al, 0.f), 1.f);
+        const float r_u = fmaxf(ru_add(elu_up(lo), -__fmul_rd(al, lo)), ru_add(elu_up(hi), -__fmul_rd(al, hi)));
+        const float x0 = al > 0.f ? fminf(fmaxf(logf(al), lo), hi) : lo;
+        const float g_x0 = rd_add(elu_dn(x0), -__fmul_ru(al, x0));
+        float slope_up;  // |ELU'(x0) - al|, rounded up
+        if (x0 >= 0.f) {
+            slope_up = ru_add(1.f, -al);
+        } else {
+            const float ex = expf(x0);
+            slope_up = ru_fma(ex, 4.7683716e-07f, fmaxf(ru_add(ex, -al), ru_add(al, -ex)));
+        }
+        const float span = fmaxf(ru_add(x0, -lo), ru_add(hi, -x0));
+        // also g >= -1 - al hi on [lo, hi] (ELU >= -1, al >= 0): the bound that
+        // stays finite when the span overflows (fmaxf drops a NaN operand)
+        const float r_l = fmaxf(rd_add(g_x0, -ru_mul(slope_up, span)), rd_add(-1.f, -__fmul_ru(al, hi)));
+        be = 0.5f * (r_u + r_l);
+        ga = fmaxf(ru_add(r_u, -be), ru_add(be, -r_l));
+    }
+    c2 = fmaf(al, c, be);
+    xi = __fmul_ru(al, xinf);
+    if (SOUND) {
+        xi = ru_fma(fabsf(c2), 1.1920929e-07f, xi);  // one rounding: <= 2^-23 |c2|
+        xi = ru_fma(__fmul_ru(al, sa), u_b2u, xi);
+    }
+}
+
+// The network's activation rule (ReLU or ELU; the same for every hidden layer).
+template <bool SOUND>
+__device__ __forceinline__ void act_rule(int act, float sa, float c, float xinf, float u_b2u, float &al, float &ga,
+                                         float &c2, float &xi) {
+    if (act == SRA_ACT_ELU) elu_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
+    else relu_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
 }
 
 // Upper bound of the summed magnitudes of a neuron's BF16 operand entries
@@ -440,7 +513,7 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
         sa = quad_scatter_ru(ps, qi);
     }
     float al, ga, c2, xi;
-    relu_rule<SOUND>(sa, cq, xq, p.ub2u, al, ga, c2, xi);
+    act_rule<SOUND>(p.act, sa, cq, xq, p.ub2u, al, ga, c2, xi);
     score[KT + nq] = ga;
     float als[4];
 #pragma unroll
@@ -662,7 +735,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 xinf = ru_fma(am, 1.1920929e-07f, xinf);  // one rounding per product
             }
             float al, ga, c2, xi;
-            relu_rule<SOUND>(am, c, xinf, p.ub2u, al, ga, c2, xi);
+            act_rule<SOUND>(p.act, am, c, xinf, p.ub2u, al, ga, c2, xi);
 #pragma unroll
             for (int d = 0; d < 3; ++d) a0[d] *= al;
             first_layer_store<H, SOUND>(x, p, a0, am, al, ga, c2, xi);

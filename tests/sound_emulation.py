@@ -3,8 +3,8 @@ radius: a study of where a sound (rounding-aware) bound has to keep its
 rounding errors.
 
 TEST INFRASTRUCTURE (numpy, FP64). It follows the same steps as the oracle
-(Proc. 1; App. A Table "affine_update_rules"; the ReLU rule of Table
-"affine_nonlinearities" with the Chebyshev slope; Sec. 3.3 truncate: K old
+(Proc. 1; App. A Table "affine_update_rules"; the ReLU and ELU rules of
+Table "affine_nonlinearities" with the Chebyshev slope; Sec. 3.3 truncate: K old
 plus the new columns scored by their L1 norm, ties to the lower index,
 dropped magnitudes added to x_inf row by row) and adds, after every dense
 layer but the first, a per-neuron radius
@@ -44,6 +44,23 @@ def _relu_rule(c, r):
     return al, be, be
 
 
+def _elu(x):
+    return np.where(x > 0, x, np.expm1(np.minimum(x, 0.0)))
+
+
+def _elu_rule(c, r):
+    """ELU's rule (App. A, reading R2): the secant slope, the secant and
+    tangent intercepts; the identity where the range is non-negative."""
+    lo, hi = c - r, c + r
+    w = hi - lo
+    a = np.where(w > 0, (_elu(hi) - _elu(lo)) / np.where(w > 0, w, 1.0), np.exp(np.minimum(lo, 0.0)))
+    ru = _elu(lo) - a * lo
+    rl = np.where(a > 0, (a - 1) - a * np.log(np.where(a > 0, a, 1.0)), -1.0)
+    b = (ru + rl) / 2
+    ident = lo >= 0
+    return np.where(ident, 1.0, a), np.where(ident, 0.0, b), np.where(ident, 0.0, ru - b)
+
+
 def _truncate(A, new, K):
     C = np.concatenate([A, new], axis=2)
     B, h, m = C.shape
@@ -58,13 +75,14 @@ def _truncate(A, new, K):
 
 
 def bound(mlp, centers, halfw, K, scheme="xinf", u=0.0, d=None, u_store=0.0):
-    """Affine-truncate bound of a ReLU MLP over boxes, with the rounding radius
-    of `scheme`. u_store > 0 adds, after each hidden activation,
+    """Affine-truncate bound of a ReLU or ELU MLP (its first activation
+    decides) over boxes, with the rounding radius of `scheme`. u_store > 0 adds, after each hidden activation,
     u_store * alpha_i * sum_k |A_ik| to x_inf: the rounding of the scaled noise
     entries when they are stored in a narrower format for the next layer
     (BF16: u_store = 2^-8). Returns (cls, lo, hi, rad): cls 1 POSITIVE,
     2 NEGATIVE, 0 UNKNOWN."""
     L, B = mlp.n_layers, len(centers)
+    rule = _elu_rule if mlp.acts[0] == 2 else _relu_rule
     c = np.asarray(centers, np.float64)
     A = np.zeros((B, 3, 3))
     A[:, [0, 1, 2], [0, 1, 2]] = np.asarray(halfw, np.float64)
@@ -85,7 +103,7 @@ def bound(mlp, centers, halfw, K, scheme="xinf", u=0.0, d=None, u_store=0.0):
             break
         esum = sum(np.abs(E).sum(2) for _, E in errs) if errs else 0.0
         r = np.abs(A).sum(2) + xi + esum + (rho if rho is not None else 0.0)
-        al, be, ga = _relu_rule(c, r)
+        al, be, ga = rule(c, r)
         if u_store > 0:
             xi = xi + u_store * np.abs(A).sum(2)  # becomes al * (...) below
         c = al * c + be

@@ -132,6 +132,7 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
         (wl.make_mlp([256] * 3, "relu", seed=32), dict(arith="truncate", K=64, precision="bf16"), 5, 777, 5),
         (wl.make_mlp([256] * 5, "relu", seed=33), dict(arith="truncate", K=64, precision="bf16_sound"), 3, 3, 9),
         (wl.make_mlp([64] * 4, "elu", seed=34), dict(arith="fixed"), 4, 900, 8),
+        (wl.make_mlp([128] * 3, "elu", seed=35), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 640, 7),
     ]
     nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
     try:

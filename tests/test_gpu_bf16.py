@@ -43,7 +43,9 @@ def run(sra, net, c, h, **kw):
     return lo.cpu().numpy().astype(np.float64), hi.cpu().numpy().astype(np.float64), cls.cpu().numpy()
 
 
-NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 4, "relu", seed=31)}
+NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 4, "relu", seed=31),
+        "elu128x4": lambda: wl.make_mlp([128] * 4, "elu", seed=35),
+        "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37)}
 
 
 @pytest.mark.parametrize("name", list(NETS))
@@ -90,7 +92,9 @@ def test_bf16_vs_oracle_excess(sra):
 
 
 SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
-           "relu256x3": lambda: wl.make_mlp([256] * 3, "relu", seed=32)}
+           "relu256x3": lambda: wl.make_mlp([256] * 3, "relu", seed=32),
+           "elu128x3": lambda: wl.make_mlp([128] * 3, "elu", seed=36),
+           "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37)}
 
 
 @pytest.mark.parametrize("name", list(SHALLOW))
@@ -154,17 +158,26 @@ def test_bf16_unsupported_shapes(sra):
     with pytest.raises(sra.SraError) as e:
         sra.bound_boxes(net, c, c, arith="fixed", precision="bf16_sound")
     assert e.value.code == sra.EUNSUPPORTED
+    with pytest.raises(sra.SraError) as e:  # the kernel's rules use the Chebyshev slope
+        sra.bound_boxes(net, c, c, arith="truncate", K=64, slope="minrange", precision="bf16_sound")
+    assert e.value.code == sra.EUNSUPPORTED
+    net.close()
+    net = sra.Net(wl.make_mlp([128] * 3, "sin", seed=2))  # sin: no tensor-core rule
+    with pytest.raises(sra.SraError) as e:
+        sra.bound_boxes(net, c, c, arith="truncate", K=64, precision="bf16")
+    assert e.value.code == sra.EUNSUPPORTED
     net.close()
 
 
-def test_bf16_plain_tracks_oracle(sra):
+@pytest.mark.parametrize("name", ["relu256x8", "elu256x3"])
+def test_bf16_plain_tracks_oracle(sra, name):
     """Plain BF16 tensor-core bounds (no rounding radius): error against the
     FP64 oracle is stated per box; it comes from the BF16 rounding of the
     noise columns (relative 2^-8 per entry, weights and centers carried as
     BF16 hi/lo pairs). Gates: radius within 2 %, center within 1e-3 of the
     scale, classes equal except where the oracle bound is within that
     tolerance of zero."""
-    mlp = wl.net_relu256x8()
+    mlp = NETS[name]()
     net = sra.Net(mlp)
     c, h = level_boxes(200, seed=9)
     lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16")

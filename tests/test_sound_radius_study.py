@@ -91,3 +91,17 @@ def test_radius_as_kept_symbols(case):
     assert unknown(cls_k) <= unknown(cls0) + 1 / 64
     # the radius only widens the exact-arithmetic bound
     assert np.all(rad_k >= rad0 * (1 - 1e-12))
+
+
+def test_emulation_elu_is_the_oracle_without_rounding():
+    """The emulation's ELU rule and truncation on an ELU network equal the
+    oracle's (the model the BF16-sound ELU gate of tests/test_gpu_bf16.py
+    uses)."""
+    mlp = wl.make_mlp([128] * 3, "elu", seed=36)
+    c, h = wl.make_boxes(96, seed=7, hw_lo=1 / 256, hw_hi=1 / 16)
+    cls0, lo0, hi0, rad0 = bound(mlp, c.astype(np.float64), h.astype(np.float64), 64)
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
+    scale = np.abs(ref["y0"]) + ref["rad"]
+    tie = ref["sel_gap"] < 1e-6
+    assert np.all(((np.abs(ref["lo"] - lo0) <= 1e-9 * scale) & (np.abs(ref["hi"] - hi0) <= 1e-9 * scale)) | tie)
+    assert np.all((cls0 == ref["cls"]) | tie)
