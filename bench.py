@@ -68,8 +68,8 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true>": {"sha1": "de669634f5a833ec72e7eadb050ab01b365e8465", "bytes": 3328256,
-                                  "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
+    "tc_bound_kernel<256,true,ReLU>": {"sha1": "d34369b92373d669c08e8105f2f146009620f713", "bytes": 3014912,
+                                       "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
                     "paper_2202_02444_gb300/csrc/tc_bound.h")
@@ -192,11 +192,11 @@ class ClockSampler:
 
 
 def tc_box_net(m):
-    """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU
-    or ELU network with one hidden width H in {128, 256} and at most 12 hidden
-    tensor-core layers, no positional encoding."""
+    """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU,
+    ELU or sin network with one hidden width H in {128, 256} and at most 12
+    hidden tensor-core layers, no positional encoding."""
     return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and len(set(m.acts)) == 1
-            and m.acts[0] in (1, 2) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
+            and m.acts[0] in (1, 2, 3) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
 
 
 def serving_nets():
@@ -321,7 +321,7 @@ def batched_phase(sra, torch, cap):
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
     # the same 64 trees with BF16-sound bounds on the tensor cores for every
-    # network that has that kernel (ReLU, one width 128 or 256, K = 64), the
+    # network that has that kernel (one width 128 or 256, K = 64), the
     # others in their autotuned FP32 form, all in the same batched rounds
     tc = [tc_box_net(m) for m in mlps]
     opts_tc = [sra.make_opts(arith="truncate", K=64, precision="bf16_sound") if t else o for t, o in zip(tc, opts)]
@@ -906,7 +906,7 @@ def main():
         peak_src = "152 SMs x 128 FP32 lanes x 2 flop x max SM clock"
     else:
         peak, bound = measured_peak("bf16_tflops", 1900.0)
-        kname = f"tc_bound_kernel<256,{'true' if args.precision == 'bf16_sound' else 'false'}> (tcgen05 BF16)"
+        kname = f"tc_bound_kernel<256,{'true' if args.precision == 'bf16_sound' else 'false'},ReLU> (tcgen05 BF16)"
         peak_src = "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS) of measured"
         bound = "tensor"
     if rank == 0:
@@ -936,7 +936,7 @@ def main():
             "roofline": {"bound": bound, "kernel": kname,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": captured_traffic("tc_bound_kernel<256,true>")
+                         "traffic": captured_traffic("tc_bound_kernel<256,true,ReLU>")
                          if args.precision == "bf16_sound" else None,
                          "kernel_ms": mean_box, "kernel_ms_alone": kern_ms,
                          "timing": "CUDA events around each timed step (bound kernel + compaction)",

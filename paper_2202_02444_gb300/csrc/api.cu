@@ -350,15 +350,15 @@ sra_status check_net(const sra_net *n) {
 }
 
 // Prepare the tensor-core path if the network has its shape: 3 inputs,
-// L-1 >= 2 hidden layers of one width H in {128, 256}, all ReLU or all ELU,
-// scalar output.
+// L-1 >= 2 hidden layers of one width H in {128, 256}, all ReLU, all ELU or
+// all sin, scalar output.
 void prepare_tc(sra_net *n, const float *params) {
     const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
     if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256)) return;
     for (int l = 1; l < L; ++l)
         if (n->widths[l] != H) return;
     const int act = n->acts[0];
-    if (act != SRA_ACT_RELU && act != SRA_ACT_ELU) return;
+    if (act != SRA_ACT_RELU && act != SRA_ACT_ELU && act != SRA_ACT_SIN) return;
     for (int l = 0; l + 1 < L; ++l)
         if (n->acts[l] != act) return;
     const int nh = L - 2;

@@ -212,20 +212,97 @@ __device__ __forceinline__ void elu_rule(float sa, float c, float xinf, float u_
     }
 }
 
-// The network's activation rule (ReLU or ELU; the same for every hidden layer).
+// Bounds of al * (x - c) for floats x, c: the difference is bracketed by its
+// two directed roundings, each product rounded outward.
+__device__ __forceinline__ void slope_times_offset(float al, float x, float c, float &p_dn, float &p_up) {
+    const float t0 = rd_add(x, -c), t1 = ru_add(x, -c);
+    p_dn = fminf(__fmul_rd(al, t0), __fmul_rd(al, t1));
+    p_up = fmaxf(__fmul_ru(al, t0), __fmul_ru(al, t1));
+}
+
+// The sin rule of App. A Table "affine_nonlinearities" (reading R3) for one
+// neuron, with the outputs of relu_rule. The slope is the FP32 one of the
+// table (from the cos range). The sound form bounds h(x) = sin(x) - al (x - c)
+// on the outward-rounded [lo, hi] (the output is al (y - c) + c2 +- ga for
+// the input form y of centre c, so c2 is the mid-point of that bound and
+// carries no rounding of its own; measuring x from c keeps the products small
+// when |c| is large, as on SIREN layers). Any slope is valid: the extremes of
+// h lie at the ends or at the critical points +-acos(al) + 2 pi k inside
+// [lo, hi], and each of those is within dx of one of the computed candidates
+// (per family the first point >= lo and the last point <= hi, clamped to
+// [lo, hi]), where dx = 2^-20 (|x| + 8) covers the FP32 error of acos, of
+// 2 pi k and of the sums. Since |h''| <= 1 and h' vanishes at a true critical
+// point x*, |h'| <= dx between x* and its candidate, so h(x*) is within dx^2
+// of h at the candidate. The ends are exact floats; sinf is within 2 ulp
+// (padded by 4 ulp of its result plus the smallest normal float). A range of
+// 2 pi or more gives al = 0, c2 = 0, ga = 1.
 template <bool SOUND>
-__device__ __forceinline__ void act_rule(int act, float sa, float c, float xinf, float u_b2u, float &al, float &ga,
-                                         float &c2, float &xi) {
-    if (act == SRA_ACT_ELU) elu_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
+__device__ __forceinline__ void sin_rule(float sa, float c, float xinf, float u_b2u, float &al, float &ga, float &c2,
+                                         float &xi) {
+    const float rad = ru_add(sa, xinf);
+    const float lo = rd_add(c, -rad), hi = ru_add(c, rad);
+    const float two_pi = 6.2831853f;
+    if (!SOUND) {
+        float be;
+        linearize<float>(SRA_ACT_SIN, SRA_SLOPE_CHEBYSHEV, lo, hi, al, be, ga);
+        c2 = fmaf(al, c, be);
+    } else if (!(ru_add(hi, -lo) < two_pi)) {
+        al = 0.f; c2 = 0.f; ga = 1.f;
+    } else {
+        float b0, g0;
+        linearize<float>(SRA_ACT_SIN, SRA_SLOPE_CHEBYSHEV, lo, hi, al, b0, g0);
+        al = fminf(fmaxf(al, -1.f), 1.f);
+        const float ep = acosf(al);
+        float cand[6];
+        cand[0] = lo;
+        cand[1] = hi;
+        cand[2] = fminf(fmaxf(ep + two_pi * ceilf((lo - ep) / two_pi), lo), hi);
+        cand[3] = fminf(fmaxf(ep + two_pi * floorf((hi - ep) / two_pi), lo), hi);
+        cand[4] = fminf(fmaxf(-ep + two_pi * ceilf((lo + ep) / two_pi), lo), hi);
+        cand[5] = fminf(fmaxf(-ep + two_pi * floorf((hi + ep) / two_pi), lo), hi);
+        float r_u = -INFINITY, r_l = INFINITY, end_dn = INFINITY, end_up = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const float x = cand[q];
+            const float sv = sinf(x);
+            float margin = ru_fma(fabsf(sv), 4.7683716e-07f, 1.17549435e-38f);
+            if (q >= 2) {
+                const float dx = ru_mul(ru_add(fabsf(x), 8.f), 9.5367432e-07f);
+                margin = ru_fma(dx, dx, margin);
+            }
+            float p_dn, p_up;
+            slope_times_offset(al, x, c, p_dn, p_up);
+            if (q < 2) { end_dn = fminf(end_dn, p_dn); end_up = fmaxf(end_up, p_up); }
+            r_u = fmaxf(r_u, ru_add(ru_add(sv, -p_dn), margin));
+            r_l = fminf(r_l, rd_add(rd_add(sv, -p_up), -margin));
+        }
+        // al (x - c) is linear in x, so its range on [lo, hi] is that of the
+        // ends, and h lies in [-1 - al (x - c), 1 - al (x - c)]
+        r_u = fminf(r_u, ru_add(1.f, -end_dn));
+        r_l = fmaxf(r_l, rd_add(-1.f, -end_up));
+        c2 = 0.5f * (r_u + r_l);
+        ga = fmaxf(ru_add(r_u, -c2), ru_add(c2, -r_l));
+    }
+    xi = __fmul_ru(fabsf(al), xinf);
+    if (SOUND) xi = ru_fma(__fmul_ru(fabsf(al), sa), u_b2u, xi);
+}
+
+// The network's activation rule (ReLU, ELU or sin; the same for every
+// hidden layer), fixed per kernel instantiation.
+template <bool SOUND, int ACT>
+__device__ __forceinline__ void act_rule(float sa, float c, float xinf, float u_b2u, float &al, float &ga, float &c2,
+                                         float &xi) {
+    if constexpr (ACT == SRA_ACT_ELU) elu_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
+    else if constexpr (ACT == SRA_ACT_SIN) sin_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
     else relu_rule<SOUND>(sa, c, xinf, u_b2u, al, ga, c2, xi);
 }
 
 // Upper bound of the summed magnitudes of a neuron's BF16 operand entries
 // after truncation: every kept entry is bf16(al * a) (at most (1 + 2^-8)
-// al |a| each, kept or not) and the neuron's own new symbol (at most
+// |al a| each, kept or not) and the neuron's own new symbol (at most
 // (1 + 2^-7) ga).
 __device__ __forceinline__ float operand_mag_bound(float al, float sa, float ga) {
-    return ru_mul(ru_add(ru_mul(al, sa), ga), 1.0078125f);
+    return ru_mul(ru_add(ru_mul(fabsf(al), sa), ga), 1.0078125f);
 }
 
 // Top-KT of the group's Ncur + H candidates (Sec. 3.3 truncate), by one
@@ -467,7 +544,7 @@ __device__ __forceinline__ float quad_scatter_ru(const float (&v)[4], int q) {
 //
 // Thread i's own neuron enters as its two center accumulators (TMEM columns
 // ccol, ccol + 1 of its lane), its bias and its |W_b| v sum xacc.
-template <int H, bool SOUND>
+template <int H, bool SOUND, int ACT>
 __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, int col0, uint32_t ccol, float bias,
                                 float xacc) {
     using Lt = Layout<H>;
@@ -513,7 +590,7 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
         sa = quad_scatter_ru(ps, qi);
     }
     float al, ga, c2, xi;
-    act_rule<SOUND>(p.act, sa, cq, xq, p.ub2u, al, ga, c2, xi);
+    act_rule<SOUND, ACT>(sa, cq, xq, p.ub2u, al, ga, c2, xi);
     score[KT + nq] = ga;
     float als[4];
 #pragma unroll
@@ -606,7 +683,7 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     store_neuron<H, SOUND>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
 }
 
-template <int H, bool SOUND>
+template <int H, bool SOUND, int ACT>
 __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
                                                             BoundOut out) {
     using Lt = Layout<H>;
@@ -735,7 +812,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
                 xinf = ru_fma(am, 1.1920929e-07f, xinf);  // one rounding per product
             }
             float al, ga, c2, xi;
-            act_rule<SOUND>(p.act, am, c, xinf, p.ub2u, al, ga, c2, xi);
+            act_rule<SOUND, ACT>(am, c, xinf, p.ub2u, al, ga, c2, xi);
 #pragma unroll
             for (int d = 0; d < 3; ++d) a0[d] *= al;
             first_layer_store<H, SOUND>(x, p, a0, am, al, ga, c2, xi);
@@ -824,7 +901,7 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             if (__syncthreads_or(*x.abort_flag != 0)) break;  // every operand read of this layer is done
             // ---- epilogue of the group's box -------------------------------
             const float xacc = ru_add(xown, xp[g * H + i]);
-            hidden_epilogue<H, SOUND>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
+            hidden_epilogue<H, SOUND, ACT>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
                                       tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
         }
         if (__syncthreads_or(*x.abort_flag != 0)) break;
@@ -952,19 +1029,37 @@ int tc_smem_bytes(int H) {
     return H == 256 ? tc::Layout<256>::ALLOC : (H == 128 ? tc::Layout<128>::ALLOC : 0);
 }
 
-template <int H, bool SOUND>
+template <int H, bool SOUND, int ACT>
 static cudaError_t launch_one(const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid, cudaStream_t st) {
     const int smem = tc_smem_bytes(H);
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc::tc_bound_kernel<H, SOUND><<<grid, 2 * H, smem, st>>>(p, src, out);
+    tc::tc_bound_kernel<H, SOUND, ACT><<<grid, 2 * H, smem, st>>>(p, src, out);
     return cudaGetLastError();
+}
+
+template <int H, int ACT>
+static cudaError_t launch_act(bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
+                              cudaStream_t st) {
+    return sound ? launch_one<H, true, ACT>(p, src, out, grid, st) : launch_one<H, false, ACT>(p, src, out, grid, st);
+}
+
+template <int H>
+static cudaError_t launch_h(bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
+                            cudaStream_t st) {
+    switch (p.act) {
+        case SRA_ACT_RELU: return launch_act<H, SRA_ACT_RELU>(sound, p, src, out, grid, st);
+        case SRA_ACT_ELU: return launch_act<H, SRA_ACT_ELU>(sound, p, src, out, grid, st);
+        case SRA_ACT_SIN: return launch_act<H, SRA_ACT_SIN>(sound, p, src, out, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tc_bound(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
                             cudaStream_t st) {
-    if (H == 256) return sound ? launch_one<256, true>(p, src, out, grid, st) : launch_one<256, false>(p, src, out, grid, st);
-    if (H == 128) return sound ? launch_one<128, true>(p, src, out, grid, st) : launch_one<128, false>(p, src, out, grid, st);
+    if (H == 256) return launch_h<256>(sound, p, src, out, grid, st);
+    if (H == 128) return launch_h<128>(sound, p, src, out, grid, st);
     return cudaErrorInvalidValue;
 }
 

@@ -24,7 +24,7 @@ struct TcParams {
     float ub2u;    // bf16 + fp32 rounding of the scaled noise entries
     float gam_out, gam_c_out;  // FP32 dot-product error factors of the output layer
     int test_stall;  // 0; > 0 (tests only): no weight copies and this many spins per bounded wait
-    int act;         // SRA_ACT_RELU or SRA_ACT_ELU: the rule of every hidden layer
+    int act;         // SRA_ACT_RELU, SRA_ACT_ELU or SRA_ACT_SIN: the rule of every hidden layer (selects the instantiation)
 };
 
 int tc_smem_bytes(int H);

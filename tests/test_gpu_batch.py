@@ -123,8 +123,8 @@ def test_batch_appends_to_counts(sra):
 
 
 def test_batch_bf16_segments_equal_lone_rounds(sra):
-    """Segments in BF16-sound and plain BF16 (their networks have the
-    tensor-core path) run beside FP32 segments in one batched round; each
+    """Segments in BF16-sound and plain BF16 (their ReLU, ELU and sin
+    networks have the tensor-core path) run beside FP32 segments in one batched round; each
     equals a lone round with the same options."""
     specs = [
         (wl.make_mlp([128] * 4, "relu", seed=31), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 1001, 6),
@@ -133,6 +133,8 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
         (wl.make_mlp([256] * 5, "relu", seed=33), dict(arith="truncate", K=64, precision="bf16_sound"), 3, 3, 9),
         (wl.make_mlp([64] * 4, "elu", seed=34), dict(arith="fixed"), 4, 900, 8),
         (wl.make_mlp([128] * 3, "elu", seed=35), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 640, 7),
+        (wl.make_mlp([256] * 3, "sin", seed=39), dict(arith="truncate", K=64, precision="bf16_sound"), 6, 513, 9),
+        (wl.make_mlp([128] * 4, "sin", seed=41), dict(arith="truncate", K=64, precision="bf16"), 5, 300, 8),
     ]
     nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
     try:

@@ -45,7 +45,9 @@ def run(sra, net, c, h, **kw):
 
 NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 4, "relu", seed=31),
         "elu128x4": lambda: wl.make_mlp([128] * 4, "elu", seed=35),
-        "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37)}
+        "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37),
+        "sin128x4": lambda: wl.make_mlp([128] * 4, "sin", seed=41),
+        "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39)}
 
 
 @pytest.mark.parametrize("name", list(NETS))
@@ -94,7 +96,12 @@ def test_bf16_vs_oracle_excess(sra):
 SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
            "relu256x3": lambda: wl.make_mlp([256] * 3, "relu", seed=32),
            "elu128x3": lambda: wl.make_mlp([128] * 3, "elu", seed=36),
-           "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37)}
+           "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37),
+           "sin128x3": lambda: wl.make_mlp([128] * 3, "sin", seed=38),
+           "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39)}
+# box half-widths: the SIREN nets (omega0 = 30 folded into the weights) need
+# smaller boxes before the oracle decides a sizeable share of them
+SHALLOW_BOXES = {"sin128x3": (1 / 1024, 1 / 128), "sin256x3": (1 / 4096, 1 / 256)}
 
 
 @pytest.mark.parametrize("name", list(SHALLOW))
@@ -108,11 +115,14 @@ def test_bf16_sound_classes_on_shallow_nets(sra, name):
     (tests/sound_emulation.py: per dense layer an a-priori product and
     accumulation error u per unit of |W| (|c| + |A|), u = 2^-16 + 17 * (2H/16)
     * 2^-23 * (1 + 2^-7); per activation the BF16 storage of the scaled noise
-    entries, 2^-8 of their magnitudes; both into x_inf), plus 1 % of the
-    decided boxes."""
+    entries, 2^-8 of their magnitudes; the first layer's FP32 dot products,
+    2^-22 of |b| + |W| |c| and 2^-23 of |W| |A|; all into x_inf), plus 1 % of
+    the decided boxes. The SIREN nets' first layers (|b| up to 17, |W| up to
+    10) make the last term matter there."""
     mlp = SHALLOW[name]()
     net = sra.Net(mlp)
-    c, h = wl.make_boxes(1021, seed=7, hw_lo=1 / 256, hw_hi=1 / 16)
+    hw_lo, hw_hi = SHALLOW_BOXES.get(name, (1 / 256, 1 / 16))
+    c, h = wl.make_boxes(1021, seed=7, hw_lo=hw_lo, hw_hi=hw_hi)
     lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
     ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
     tie = ref["sel_gap"] < 1e-2
@@ -122,7 +132,7 @@ def test_bf16_sound_classes_on_shallow_nets(sra, name):
     assert not np.any(((cls == 1) & (ref["cls"] == 2)) | ((cls == 2) & (ref["cls"] == 1)))
     H = mlp.widths[1]
     u = (2.0 ** -16 + 17 * (2 * H // 16) * 2.0 ** -23 * (1 + 2.0 ** -7)) * 1.001
-    mcls = emulate(mlp, c, h, 64, "xinf", u, u_store=2.0 ** -8)[0]
+    mcls = emulate(mlp, c, h, 64, "xinf", u, u_store=2.0 ** -8, u_first=2.0 ** -22)[0]
     dec = ref["cls"] != 0
     lost, lost_model = dec & (cls == 0), dec & (mcls == 0)
     print(f"{name}: oracle UNKNOWN {np.mean(~dec):.4f}, BF16-sound UNKNOWN {np.mean(cls == 0):.4f} "
@@ -162,14 +172,16 @@ def test_bf16_unsupported_shapes(sra):
         sra.bound_boxes(net, c, c, arith="truncate", K=64, slope="minrange", precision="bf16_sound")
     assert e.value.code == sra.EUNSUPPORTED
     net.close()
-    net = sra.Net(wl.make_mlp([128] * 3, "sin", seed=2))  # sin: no tensor-core rule
+    mixed = wl.make_mlp([128] * 3, "relu", seed=2)
+    mixed.acts[1] = wl.ACT_ELU  # one rule per network on the tensor cores
+    net = sra.Net(mixed)
     with pytest.raises(sra.SraError) as e:
         sra.bound_boxes(net, c, c, arith="truncate", K=64, precision="bf16")
     assert e.value.code == sra.EUNSUPPORTED
     net.close()
 
 
-@pytest.mark.parametrize("name", ["relu256x8", "elu256x3"])
+@pytest.mark.parametrize("name", ["relu256x8", "elu256x3", "sin256x3"])
 def test_bf16_plain_tracks_oracle(sra, name):
     """Plain BF16 tensor-core bounds (no rounding radius): error against the
     FP64 oracle is stated per box; it comes from the BF16 rounding of the

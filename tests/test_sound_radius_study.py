@@ -93,11 +93,12 @@ def test_radius_as_kept_symbols(case):
     assert np.all(rad_k >= rad0 * (1 - 1e-12))
 
 
-def test_emulation_elu_is_the_oracle_without_rounding():
-    """The emulation's ELU rule and truncation on an ELU network equal the
-    oracle's (the model the BF16-sound ELU gate of tests/test_gpu_bf16.py
-    uses)."""
-    mlp = wl.make_mlp([128] * 3, "elu", seed=36)
+@pytest.mark.parametrize("act,seed", [("elu", 36), ("sin", 38)])
+def test_emulation_elu_sin_is_the_oracle_without_rounding(act, seed):
+    """The emulation's ELU and sin rules and truncation on an ELU and a
+    SIREN network equal the oracle's (the model the BF16-sound ELU and sin
+    gates of tests/test_gpu_bf16.py use)."""
+    mlp = wl.make_mlp([128] * 3, act, seed=seed)
     c, h = wl.make_boxes(96, seed=7, hw_lo=1 / 256, hw_hi=1 / 16)
     cls0, lo0, hi0, rad0 = bound(mlp, c.astype(np.float64), h.astype(np.float64), 64)
     ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
@@ -105,3 +106,19 @@ def test_emulation_elu_is_the_oracle_without_rounding():
     tie = ref["sel_gap"] < 1e-6
     assert np.all(((np.abs(ref["lo"] - lo0) <= 1e-9 * scale) & (np.abs(ref["hi"] - hi0) <= 1e-9 * scale)) | tie)
     assert np.all((cls0 == ref["cls"]) | tie)
+
+
+def test_emulation_sin_rule_is_the_oracle_rule():
+    """The emulation's vectorised sin rule against the oracle's, range by
+    range: ranges of every length up to 3 pi (at and past 2 pi the slope is
+    0), ranges with an end on a critical point or a multiple of pi, and
+    ranges far from the origin."""
+    from tests.sound_emulation import _sin_rule
+    rng = np.random.default_rng(5)
+    c = np.concatenate([rng.uniform(-40, 40, 400), np.pi * np.arange(-6, 7), np.full(6, 0.5 * np.pi)])
+    r = np.concatenate([rng.uniform(0, 1.5 * np.pi, 400), np.full(13, 0.3), [0.0, 1e-9, np.pi / 2, np.pi, 1.2 * np.pi,
+                                                                               3.0]])
+    a, b, g = _sin_rule(c, r)
+    for i in range(len(c)):
+        ra, rb, rg = oracle.linearize(wl.ACT_SIN, c[i] - r[i], c[i] + r[i])
+        assert abs(a[i] - ra) <= 1e-12 and abs(b[i] - rb) <= 1e-9 * (1 + abs(c[i])) and abs(g[i] - rg) <= 1e-9
