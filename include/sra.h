@@ -352,11 +352,13 @@ sra_status sra_eval(const sra_net *net, const float *x, int64_t n, float *out, v
  * allocates nothing.
  * Limits: n_in <= SRA_NOALLOC_MAX_NODES, else SRA_EINVAL (nothing queued).
  * Unsupported options, each SRA_EUNSUPPORTED (nothing queued): precision
- * SRA_PREC_BF16_SOUND or SRA_PREC_BF16 (FP32 and FP64 only), and
- * opts->converge (the convergence test of Proc. 3).
+ * SRA_PREC_BF16_SOUND or SRA_PREC_BF16 (FP32 and FP64 only),
+ * opts->converge (the convergence test of Proc. 3), and affine-full on a
+ * network whose noise matrix does not fit shared memory (positional
+ * encoding, or widths past 64: that form keeps its state in device memory).
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and keeps it for the rest of the process; make that
- * first call before any stream capture. The address is not looked up again,
+ * (cudaGetSymbolAddress) and keeps it for the rest of the process. The
+ * address is not looked up again,
  * so after cudaDeviceReset (or any teardown of the device's primary context)
  * this entry point must not be used in the same process. All calls share
  * the array, which keeps the previous call's contents (each call clears what
