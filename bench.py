@@ -193,10 +193,10 @@ class ClockSampler:
 
 def tc_box_net(m):
     """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU,
-    ELU or sin network with one hidden width H in {128, 256} and at most 12
+    ELU or sin network with one hidden width H in {128, 256, 512} and at most 12
     hidden tensor-core layers, no positional encoding."""
     return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and len(set(m.acts)) == 1
-            and m.acts[0] in (1, 2, 3) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256))
+            and m.acts[0] in (1, 2, 3) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256, 512))
 
 
 def serving_nets():
@@ -321,7 +321,7 @@ def batched_phase(sra, torch, cap):
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
     # the same 64 trees with BF16-sound bounds on the tensor cores for every
-    # network that has that kernel (one width 128 or 256, K = 64), the
+    # network that has that kernel (one width 128, 256 or 512, K = 64), the
     # others in their autotuned FP32 form, all in the same batched rounds
     tc = [tc_box_net(m) for m in mlps]
     opts_tc = [sra.make_opts(arith="truncate", K=64, precision="bf16_sound") if t else o for t, o in zip(tc, opts)]
@@ -414,7 +414,42 @@ def policies_phase(sra, torch, dev):
                                          "unknown_frac": float((cl == 0).float().mean()),
                                          "flop_per_box": flop, "tflops": flop * Bw / (ms / 1e3) / 1e12}
     net.close()
+    res["tc_widths"] = tc_widths_phase(sra, torch, dev, timed)
     return res
+
+
+def tc_widths_phase(sra, torch, dev, timed):
+    """The tensor-core bound kernel at each width it serves (3-[H]x4-1 ReLU,
+    He init, seed 51; H = 128 and 256 bound two boxes per CTA, H = 512 one),
+    affine-truncate K = 64 on 32,768 boxes (half-widths log-U[1/1024, 1/64]),
+    against the FP32 SIMT kernel on the same boxes."""
+    B = 1 << 15
+    c, h = wl.make_boxes(B, seed=3, hw_lo=1 / 1024, hw_hi=1 / 64)
+    C_, H_ = torch.from_numpy(c).to(dev), torch.from_numpy(h).to(dev)
+    peak = measured_peak("bf16_tflops", 1900.0)[0]
+    out = {"workload": f"ReLU 3-[H]x4-1 (He init, seed 51), {B} boxes, half-widths log-U[1/1024, 1/64], "
+                       "affine-truncate K=64", "peak_tflops": peak, "widths": {}}
+    for H in (128, 256, 512):
+        mlp = wl.make_mlp([H] * 4, "relu", seed=51)
+        net = sra.Net(mlp)
+        flop = box_flops(mlp, 64)
+        row = {"flop_per_box": flop}
+        for prec in ("fp32", "bf16", "bf16_sound"):
+            o = sra.make_opts(arith="truncate", K=64, precision=prec)
+            try:
+                ms, (lo, hi, cl) = timed(lambda: sra.bound_boxes(net, C_, H_, opts=o))
+            except sra.SraError as e:  # the SIMT engine's per-box thread budget
+                row[prec] = {"unsupported": str(e)}
+                continue
+            if prec != "fp32":
+                sra.sync_status(net)
+            tf = flop * B / (ms / 1e3) / 1e12
+            row[prec] = {"box_evals_per_s": B / (ms / 1e3), "tflops": tf,
+                         "frac_of_bf16_peak": tf / peak if prec != "fp32" else None,
+                         "unknown_frac": float((cl == 0).float().mean())}
+        out["widths"][str(H)] = row
+        net.close()
+    return out
 
 
 def octree_phase(sra, torch, dev, net, depth=10, level_cap=1 << 21, K=64):

@@ -293,8 +293,9 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
     if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || o->K != 64 ||
                  o->slope != SRA_SLOPE_CHEBYSHEV))
         return fail(SRA_EUNSUPPORTED,
-                    "BF16 tensor-core bounds need a 3 -> H x L -> 1 ReLU or ELU network (H = 128 or 256, at most %d "
-                    "hidden tensor-core layers) with affine-truncate K = 64 and the Chebyshev slope",
+                    "BF16 tensor-core bounds need a 3 -> H x L -> 1 network with one activation (ReLU, ELU or sin; "
+                    "H = 128, 256 or 512, at most %d hidden tensor-core layers) with affine-truncate K = 64 and the "
+                    "Chebyshev slope",
                     kMaxTcLayers);
     const bool fp64 = o->precision == SRA_PREC_FP64;
     const bool recheck = o->recheck && !fp64;
@@ -309,7 +310,8 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
     }
     sra_status r = SRA_OK;
     if (bf16) {
-        const long long tiles = (count + 1) / 2;
+        const int nb = tc_boxes_per_tile(n->tc_H);
+        const long long tiles = (count + nb - 1) / nb;
         long long grid = num_sms();
         if (grid > tiles) grid = tiles;
         if (grid < 1) grid = 1;
@@ -350,11 +352,11 @@ sra_status check_net(const sra_net *n) {
 }
 
 // Prepare the tensor-core path if the network has its shape: 3 inputs,
-// L-1 >= 2 hidden layers of one width H in {128, 256}, all ReLU, all ELU or
-// all sin, scalar output.
+// L-1 >= 2 hidden layers of one width H in {128, 256, 512}, all ReLU, all ELU
+// or all sin, scalar output.
 void prepare_tc(sra_net *n, const float *params) {
     const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
-    if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256)) return;
+    if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256 && H != 512)) return;
     for (int l = 1; l < L; ++l)
         if (n->widths[l] != H) return;
     const int act = n->acts[0];
@@ -1123,7 +1125,8 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
                  BoundOut bo;
                  memset(&bo, 0, sizeof bo);
                  bo.cls = ds[s].out.cls;
-                 const long long tiles = (segs[s].n + 1) / 2;
+                 const int nb = tc_boxes_per_tile(n->tc_H);
+                 const long long tiles = (segs[s].n + nb - 1) / nb;
                  long long grid = num_sms();
                  if (grid > tiles) grid = tiles;
                  cudaError_t e = launch_tc_bound(n->tc_H, opts[segs[s].net].precision == SRA_PREC_BF16_SOUND, n->tcp,

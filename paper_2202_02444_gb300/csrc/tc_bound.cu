@@ -1,26 +1,29 @@
 // BF16-sound RangeBound on the tensor cores (tcgen05 + TMEM + TMA).
 //
-// Network shape served: 3 -> H -> ... -> H -> 1 ReLU or ELU MLP (H = 128 or 256),
-// affine-truncate with K = 64 kept noise symbols (Sec. 3.3), the dense layers
-// of App. A Table "affine_update_rules" on tensor cores. One persistent CTA per
-// SM runs the whole network for a tile of NB = 2 boxes with 2H threads: thread
-// group g (H threads, one per neuron) owns box g, so the two boxes' SIMT work
-// runs concurrently. The per-box affine state never leaves the SM:
-//   * operand B of every hidden layer: the 2 x 64 noise columns (BF16) and a
+// Network shape served: 3 -> H -> ... -> H -> 1 ReLU, ELU or sin MLP (H = 128,
+// 256 or 512), affine-truncate with K = 64 kept noise symbols (Sec. 3.3), the
+// dense layers of App. A Table "affine_update_rules" on tensor cores. One
+// persistent CTA per SM runs the whole network for a tile of NB boxes with
+// NB x H threads (NB = 2 for H <= 256, 1 for H = 512): thread group g (H
+// threads, one per neuron) owns box g, so two boxes' SIMT work runs
+// concurrently. The per-box affine state never leaves the SM:
+//   * operand B of every hidden layer: the NB x 64 noise columns (BF16) and a
 //     16-column chunk holding each box's center as a BF16 hi/lo pair, written
 //     by the epilogue threads in the K-major 128-byte-swizzled layout; the
-//     chunk follows the noise rows of each K slice, so one MMA of N = 144
-//     covers both;
+//     chunk follows the noise rows of each K slice, so one MMA of N = NB x 64
+//     + 16 covers both;
 //   * operand A: W as BF16 hi + lo (W = W_b + W_r + rho, |rho| <= u_b^2 |W|),
-//     streamed per 64-wide K slice by TMA into a two-stage ring (lane 0 of
-//     the last warp issues the copies; lane 0 of warp m of group m issues
-//     the MMAs of M tile m, so no MMA issue waits on a refill);
+//     streamed per 64-wide K slice (at H = 512 per half of its M tiles) by
+//     TMA into a two-stage ring (lane 0 of the last warp issues the copies;
+//     one thread per M tile issues that tile's MMAs, so no MMA issue waits on
+//     a refill);
 //   * D = (W_b + W_r) [X | c_hi c_lo] accumulates in TMEM (FP32);
 //   * x_inf' >= |W| v is accumulated by the SIMT threads from the resident
 //     W_b slice with round-up FMAs (|W| <= |W_b| / (1 - u_b));
 //   * epilogue, one thread per neuron (tcgen05.ld of its TMEM row): outward
-//     rounded range, the ReLU or ELU rule, truncation to the 64 largest columns, and
-//     the a-priori rounding radius of every FP operation folded into x_inf.
+//     rounded range, the activation rule, truncation to the 64 largest
+//     columns, and the a-priori rounding radius of every FP operation folded
+//     into x_inf.
 // The first layer (3 inputs) and the output layer (1 output) run on the SIMT
 // cores with directed rounding. Every bounded wait that runs out writes a
 // status word and the CTA leaves through its normal exit (TMEM freed).
@@ -33,23 +36,27 @@
 namespace sra {
 namespace tc {
 
-constexpr int NB = 2;        // boxes per tile (one thread group each)
 constexpr int KT = 64;       // kept noise symbols per box
-constexpr int NA = NB * KT;  // noise columns per tile (MMA N)
 constexpr int NCC = 16;      // center-chunk columns (MMA N)
-constexpr int TM_STRIDE = 256;  // TMEM columns per M tile: NA noise then NCC center accumulators
 constexpr int NPART = 4;     // partial sums per output-layer dot product
 constexpr uint32_t kSpin = 1u << 22;
 
 template <int H> struct Layout {
+    static constexpr int NB = H == 512 ? 1 : 2;  // boxes per tile (one thread group each)
+    static constexpr int NT = NB * H;            // threads per CTA
+    static constexpr int NA = NB * KT;           // noise columns per tile
     static constexpr int MT = H / 128;   // M tiles per layer
     static constexpr int S = H / 64;     // K slices per layer
+    // TMEM columns per M tile: NA noise then NCC center accumulators
+    static constexpr int TM_STRIDE = H == 512 ? 128 : 256;
+    static constexpr int UPS = H == 512 ? 2 : 1;  // ring units per K slice
+    static constexpr int MPU = MT / UPS;          // M tiles per ring unit
     static constexpr int TILE = 128 * 128;                  // bytes of one 128 x 64 bf16 tile
-    static constexpr int STAGE = 2 * MT * TILE;             // W_b and W_r tiles of one K slice
+    static constexpr int STAGE = 2 * MPU * TILE;            // W_b and W_r tiles of one unit
     static constexpr int W_OFF = 0;
     static constexpr int XA_OFF = 2 * STAGE;
     // operand B, per 64-wide K slice: NA noise rows then NCC center rows,
-    // so one MMA of N = NA + NCC covers both (slice stride 18 KB)
+    // so one MMA of N = NA + NCC covers both (slice stride (NA + NCC) x 128 B)
     static constexpr int XA_SLICE = (NA + NCC) * 128;
     static constexpr int XC_OFF = XA_OFF + NA * 128;
     static constexpr int XC_SLICE = XA_SLICE;
@@ -64,13 +71,18 @@ template <int H> struct Layout {
     static constexpr int BOX_OFF = WOUT_OFF + H * 4;                 // box c/h [NB][8]
     static constexpr int XP_OFF = BOX_OFF + NB * 8 * 4;              // |W_b| v partials [NB][H]
     static constexpr int NCH = (KT + H + 31) / 32;                    // candidate chunks of 32
-    static constexpr int KM_OFF = XP_OFF + NB * H * 4;               // kept masks [NB][16]
-    static constexpr int NEW_OFF = KM_OFF + NB * 16 * 4;             // newlist[NB][KT]
+    static constexpr int KMW = NCH <= 16 ? 16 : 32;                  // kept-mask words per box
+    static constexpr int KM_OFF = XP_OFF + NB * H * 4;               // kept masks [NB][KMW]
+    static constexpr int NEW_OFF = KM_OFF + NB * KMW * 4;            // newlist[NB][KT]
     static constexpr int BAR_OFF = ((NEW_OFF + NB * KT * 4) + 15) & ~15;   // 5 mbarriers
     static constexpr int MISC_OFF = BAR_OFF + 64;  // tmem slot, abort, nnew[NB], sel[NB][2]
     static constexpr int DUMMY_OFF = MISC_OFF + 64;  // 32 x 16 B sink for dropped columns' stores
     static constexpr int BYTES = DUMMY_OFF + 512;
     static constexpr int ALLOC = BYTES + 1024;     // + alignment slack
+    static_assert(MPU * UPS == MT && NA + NCC <= TM_STRIDE && MT * TM_STRIDE <= 512, "TMEM columns");
+    static_assert(NCH <= KMW && NB <= 2, "kept masks");
+    static_assert(XA_OFF % 1024 == 0 && XA_SLICE % 1024 == 0 && XC_OFF % 1024 == 0, "operand alignment");
+    static_assert(ALLOC <= 232448, "shared memory");
 };
 
 // ---- directed-rounding helpers ----------------------------------------------
@@ -329,7 +341,7 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
     const int g = x.g, lane = x.lane;
     const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     const float *part = (const float *)(x.smem + Lt::PART_OFF) + g * NW * KT;
-    uint32_t *km = (uint32_t *)(x.smem + Lt::KM_OFF) + g * 16;
+    uint32_t *km = (uint32_t *)(x.smem + Lt::KM_OFF) + g * Lt::KMW;
     int *newlist = (int *)(x.smem + Lt::NEW_OFF) + g * KT;
     int *nnew_slot = (int *)(x.smem + Lt::MISC_OFF + 16) + g;
     const int C = Ncur + H;
@@ -410,7 +422,7 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
 // Kept flag of candidate c of the group's box (after select_topk and a group_sync).
 template <int H> __device__ __forceinline__ bool cand_kept(const Ctx &x, int c) {
     using Lt = Layout<H>;
-    const uint32_t *km = (const uint32_t *)(x.smem + Lt::KM_OFF) + x.g * 16;
+    const uint32_t *km = (const uint32_t *)(x.smem + Lt::KM_OFF) + x.g * Lt::KMW;
     return (km[c >> 5] >> (c & 31)) & 1u;
 }
 
@@ -492,7 +504,7 @@ __device__ void first_layer_store(const Ctx &x, const TcParams &p, const float (
     group_sync(g, H);
     select_topk<H>(x, 3);
     group_sync(g, H);
-    const uint32_t km0 = ((const uint32_t *)(x.smem + Lt::KM_OFF))[g * 16];
+    const uint32_t km0 = ((const uint32_t *)(x.smem + Lt::KM_OFF))[g * Lt::KMW];
     unsigned char *XA = x.smem + Lt::XA_OFF + (i >> 6) * Lt::XA_SLICE;
     const uint32_t kk = (uint32_t)(i & 63);
     float dropped = 0.f;
@@ -625,7 +637,7 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     group_sync(g, H);
     select_topk<H>(x, KT);
     group_sync(g, H);
-    const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * 16;
+    const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * Lt::KMW;
     const unsigned long long kept = ((unsigned long long)kmw[1] << 32) | kmw[0];
     // dropped magnitudes per neuron (reduce-scattered over the quad, rounded
     // up) to x_inf: 0/1 masks times |a|, exact products
@@ -684,10 +696,10 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
 }
 
 template <int H, bool SOUND, int ACT>
-__global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
-                                                            BoundOut out) {
+__global__ void __launch_bounds__(Layout<H>::NT, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
+                                                                    BoundOut out) {
     using Lt = Layout<H>;
-    constexpr int NT = 2 * H;
+    constexpr int NT = Lt::NT, NB = Lt::NB, NA = Lt::NA, TM_STRIDE = Lt::TM_STRIDE;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Ctx x;
     x.smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -702,16 +714,21 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     x.status = p.status;
     const int tid = x.tid, g = x.g, i = x.i;
     const int warp = tid >> 5;
-    // M tile m's MMAs are issued by lane 0 of warp m of group m (warps 0 and
-    // 9: two different schedulers); each issuer commits to the stage and
-    // accumulator barriers
+    // M tile m's MMAs are issued by one thread: with two groups lane 0 of
+    // warp m of group m (warps 0 and 9: two different schedulers), with one
+    // group lane 0 of warp m; each issuer commits to the stage barrier of
+    // every ring unit holding its tile and to the accumulator barrier
     constexpr int ISSUERS = Lt::MT;
-    const bool issuer = (i == 32 * g) && g < ISSUERS;
+    const int my_m = NB == 2 ? g : (i >> 5);
+    const bool issuer = NB == 2 ? (i == 32 * g && g < ISSUERS) : (x.lane == 0 && my_m < ISSUERS);
+    // a stage is free once the issuers of its unit's M tiles have committed
+    // and every warp that reads the unit's W_b tiles (for |W_b| v) has arrived
+    constexpr int STAGE_ARRIVALS = Lt::MPU + NT / 32 / Lt::UPS;
     if (tid == 0) {
         ptx::mbar_init(&x.bars[0], 1);
         ptx::mbar_init(&x.bars[1], 1);
-        ptx::mbar_init(&x.bars[2], ISSUERS + NT / 32);
-        ptx::mbar_init(&x.bars[3], ISSUERS + NT / 32);
+        ptx::mbar_init(&x.bars[2], STAGE_ARRIVALS);
+        ptx::mbar_init(&x.bars[3], STAGE_ARRIVALS);
         ptx::mbar_init(&x.bars[4], ISSUERS);
         ptx::fence_mbar_init();
         *x.abort_flag = 0;
@@ -733,39 +750,44 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
     const long long n = src.n;
     const long long ntiles = (n + NB - 1) / NB;
     uint32_t gring = 0, accn = 0;
-    // weight K slices stream through the ring in one global order (layer 1..L-2
-    // of every tile this CTA takes); the producer thread issues them up to two
-    // ahead of the consumers, across layer and tile boundaries, and never past
-    // the CTA's last slice
+    // weight units (a K slice, or at H = 512 half of its M tiles) stream
+    // through the ring in one global order (layer 1..L-2 of every tile this
+    // CTA takes); the producer thread issues them up to two ahead of the
+    // consumers, across layer and tile boundaries, and never past the CTA's
+    // last unit
     const int NL = p.L - 2;
     const long long my_tiles = ntiles > (long long)blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const uint32_t total_slices = (uint32_t)(my_tiles * NL * Lt::S);
+    const uint32_t total_units = (uint32_t)(my_tiles * NL * Lt::S * Lt::UPS);
     // the copies are issued by lane 0 of the last warp, so that a refill,
     // which waits for the MMAs that read the stage, never holds up the
     // issue of the next slice's MMAs
     constexpr int PRODUCER = NT - 32;
     uint32_t gload = 0;
-    int ld_layer = 1, ld_slice = 0;
+    int ld_layer = 1, ld_slice = 0, ld_half = 0;
     // bounded-wait budget; a test setting (p.test_stall > 0) also switches the
     // copies off, so that every wait on a full stage runs out with nothing in
     // flight (no copy, no MMA) and the CTA leaves through its normal exit
     const uint32_t spins = p.test_stall > 0 ? (uint32_t)p.test_stall : kSpin;
     auto issue_upto = [&](uint32_t target) {  // the producer thread
         if (p.test_stall > 0) return;
-        while (gload < target && gload < total_slices && !*x.abort_flag) {
+        while (gload < target && gload < total_units && !*x.abort_flag) {
             const uint32_t gg = gload, st = gg & 1u;
             if (!ptx::mbar_wait(&x.bars[2 + st], ((gg >> 1) & 1u) ^ 1u, spins)) { fail(x, p, 3); return; }
             unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
             ptx::mbar_arrive_expect_tx(&x.bars[st], Lt::STAGE);
             const CUtensorMap *mb = &p.wb[ld_layer - 1], *mr = &p.wr[ld_layer - 1];
-            for (int m = 0; m < Lt::MT; ++m) {
-                ptx::tma_load_2d(base + m * Lt::TILE, mb, ld_slice * 64, m * 128, &x.bars[st]);
-                ptx::tma_load_2d(base + (Lt::MT + m) * Lt::TILE, mr, ld_slice * 64, m * 128, &x.bars[st]);
+            for (int mm = 0; mm < Lt::MPU; ++mm) {
+                const int m = ld_half * Lt::MPU + mm;
+                ptx::tma_load_2d(base + mm * Lt::TILE, mb, ld_slice * 64, m * 128, &x.bars[st]);
+                ptx::tma_load_2d(base + (Lt::MPU + mm) * Lt::TILE, mr, ld_slice * 64, m * 128, &x.bars[st]);
             }
             ++gload;
-            if (++ld_slice == Lt::S) {
-                ld_slice = 0;
-                if (++ld_layer > NL) ld_layer = 1;
+            if (++ld_half == Lt::UPS) {
+                ld_half = 0;
+                if (++ld_slice == Lt::S) {
+                    ld_slice = 0;
+                    if (++ld_layer > NL) ld_layer = 1;
+                }
             }
         }
     };
@@ -826,83 +848,111 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
             float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;  // rounded-up |W_b| v partials, boxes 0 and 1
             const uint32_t g0 = gring;
             if (tid == PRODUCER) issue_upto(g0 + 2);  // no-op when prefetched during the last epilogue
-            const float *vg = (const float *)(x.smem + Lt::V_OFF) + g * H;
             for (int s = 0; s < Lt::S; ++s) {
-                const uint32_t gg = g0 + (uint32_t)s, st = gg & 1u, par = (gg >> 1) & 1u;
-                if (!ptx::mbar_wait(&x.bars[st], par, spins)) fail(x, p, 4);
-                unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
-                if (issuer && !*x.abort_flag) {
-                    ptx::tc_fence_after();
-                    const uint32_t ia = ptx::idesc_bf16(128, NA + NCC);
-                    for (int ks = 0; ks < 4; ++ks) {
-                        const uint32_t acc = (s | ks) ? 1u : 0u;
-                        const uint64_t bA =
-                            ptx::desc_kmajor_sw128(ptx::smem_u32(x.smem + Lt::XA_OFF + s * Lt::XA_SLICE)) + 2 * ks;
-                        {
-                            const int m = g;
-                            const uint64_t aB = ptx::desc_kmajor_sw128(ptx::smem_u32(base + m * Lt::TILE)) + 2 * ks;
+#pragma unroll
+                for (int hf = 0; hf < Lt::UPS; ++hf) {
+                    const uint32_t gg = g0 + (uint32_t)(s * Lt::UPS + hf), st = gg & 1u, par = (gg >> 1) & 1u;
+                    // this thread reads the unit's W_b tile of its M tile; it issues the unit's MMAs of its tile
+                    const bool mine = Lt::UPS == 1 || m_of_thread / Lt::MPU == hf;
+                    const bool my_mma = issuer && my_m / Lt::MPU == hf;
+                    if (mine || my_mma)
+                        if (!ptx::mbar_wait(&x.bars[st], par, spins)) fail(x, p, 4);
+                    unsigned char *base = x.smem + Lt::W_OFF + st * Lt::STAGE;
+                    if (my_mma && !*x.abort_flag) {
+                        ptx::tc_fence_after();
+                        const uint32_t ia = ptx::idesc_bf16(128, NA + NCC);
+                        const int mm = my_m - hf * Lt::MPU;  // the tile's place in the unit
+                        for (int ks = 0; ks < 4; ++ks) {
+                            const uint32_t acc = (s | ks) ? 1u : 0u;
+                            const uint64_t bA =
+                                ptx::desc_kmajor_sw128(ptx::smem_u32(x.smem + Lt::XA_OFF + s * Lt::XA_SLICE)) + 2 * ks;
+                            const uint64_t aB = ptx::desc_kmajor_sw128(ptx::smem_u32(base + mm * Lt::TILE)) + 2 * ks;
                             const uint64_t aR =
-                                ptx::desc_kmajor_sw128(ptx::smem_u32(base + (Lt::MT + m) * Lt::TILE)) + 2 * ks;
-                            ptx::mma_bf16(x.tmem + m * TM_STRIDE, aB, bA, ia, acc);
-                            ptx::mma_bf16(x.tmem + m * TM_STRIDE, aR, bA, ia, 1u);
+                                ptx::desc_kmajor_sw128(ptx::smem_u32(base + (Lt::MPU + mm) * Lt::TILE)) + 2 * ks;
+                            ptx::mma_bf16(x.tmem + my_m * TM_STRIDE, aB, bA, ia, acc);
+                            ptx::mma_bf16(x.tmem + my_m * TM_STRIDE, aR, bA, ia, 1u);
+                        }
+                        ptx::mma_commit(&x.bars[2 + st]);
+                        if (s + 1 == Lt::S) ptx::mma_commit(&x.bars[4]);
+                    }
+                    if constexpr (NB == 2) {
+                        // x_inf' += |W_b| v from the resident slice: thread (g, i) takes
+                        // row i over inputs 32 g .. 32 g + 31 of the slice for both boxes
+                        // (one read and unpack of each weight), in four 8-input chunks
+                        const int r = i & 127;
+                        const unsigned char *row = base + m_of_thread * Lt::TILE + r * 128;
+                        const float *v0 = (const float *)(x.smem + Lt::V_OFF) + s * 64;
+                        const float *v1 = v0 + H;
+                        // the MMA-issuing warps leave their last chunk to the other
+                        // group's warp over the same rows, which sums it into the
+                        // same row's partials (every partial rounded up)
+                        const bool light = x.wg == g && g < ISSUERS;
+                        const bool heavy = x.wg == 1 - g && 1 - g < ISSUERS;
+#pragma unroll
+                        for (int cc = 0; cc < 5; ++cc) {
+                            if ((cc == 3 && light) || (cc == 4 && !heavy)) continue;
+                            const int ch = cc < 4 ? 4 * g + cc : 4 * (1 - g) + 3;
+                            const uint4 q = *(const uint4 *)(row + (((ch ^ (r & 7)) & 7) << 4));
+                            const float4 a0 = *(const float4 *)(v0 + ch * 8), a1 = *(const float4 *)(v0 + ch * 8 + 4);
+                            const float4 b0 = *(const float4 *)(v1 + ch * 8), b1 = *(const float4 *)(v1 + ch * 8 + 4);
+                            const uint32_t wq[4] = {q.x, q.y, q.z, q.w};
+                            const float va[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                            const float vb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                            for (int e2 = 0; e2 < 4; ++e2) {
+                                // |w| of the pair as floats (bf16 bits in the high half)
+                                const float wlo = __uint_as_float((wq[e2] & 0x7fffu) << 16);
+                                const float whi = __uint_as_float(wq[e2] & 0x7fff0000u);
+                                xa0 = ru_fma(wlo, va[2 * e2], xa0);
+                                xa1 = ru_fma(whi, va[2 * e2 + 1], xa1);
+                                xb0 = ru_fma(wlo, vb[2 * e2], xb0);
+                                xb1 = ru_fma(whi, vb[2 * e2 + 1], xb1);
+                            }
+                        }
+                    } else if (mine) {
+                        // one box: thread i takes row i over the slice's 64 inputs
+                        const int r = i & 127;
+                        const unsigned char *row = base + (m_of_thread - hf * Lt::MPU) * Lt::TILE + r * 128;
+                        const float *v0 = (const float *)(x.smem + Lt::V_OFF) + s * 64;
+#pragma unroll
+                        for (int ch = 0; ch < 8; ++ch) {
+                            const uint4 q = *(const uint4 *)(row + (((ch ^ (r & 7)) & 7) << 4));
+                            const float4 a0 = *(const float4 *)(v0 + ch * 8), a1 = *(const float4 *)(v0 + ch * 8 + 4);
+                            const uint32_t wq[4] = {q.x, q.y, q.z, q.w};
+                            const float va[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+                            for (int e2 = 0; e2 < 4; ++e2) {
+                                const float wlo = __uint_as_float((wq[e2] & 0x7fffu) << 16);
+                                const float whi = __uint_as_float(wq[e2] & 0x7fff0000u);
+                                xa0 = ru_fma(wlo, va[2 * e2], xa0);
+                                xa1 = ru_fma(whi, va[2 * e2 + 1], xa1);
+                            }
                         }
                     }
-                    ptx::mma_commit(&x.bars[2 + st]);
-                    if (s + 1 == Lt::S) ptx::mma_commit(&x.bars[4]);
+                    __syncwarp();
+                    if (mine && x.lane == 0) ptx::mbar_arrive(&x.bars[2 + st]);
+                    if (tid == PRODUCER) issue_upto(gg + 3);
                 }
-                // x_inf' += |W_b| v from the resident slice: thread (g, i) takes
-                // row i over inputs 32 g .. 32 g + 31 of the slice for both boxes
-                // (one read and unpack of each weight), in four 8-input chunks
-                {
-                    const int r = i & 127;
-                    const unsigned char *row = base + m_of_thread * Lt::TILE + r * 128;
-                    const float *v0 = (const float *)(x.smem + Lt::V_OFF) + s * 64;
-                    const float *v1 = v0 + H;
-                    // the MMA-issuing warps leave their last chunk to the other
-                    // group's warp over the same rows, which sums it into the
-                    // same row's partials (every partial rounded up)
-                    const bool light = x.wg == g && g < ISSUERS;
-                    const bool heavy = x.wg == 1 - g && 1 - g < ISSUERS;
-#pragma unroll
-                    for (int cc = 0; cc < 5; ++cc) {
-                        if ((cc == 3 && light) || (cc == 4 && !heavy)) continue;
-                        const int ch = cc < 4 ? 4 * g + cc : 4 * (1 - g) + 3;
-                        const uint4 q = *(const uint4 *)(row + (((ch ^ (r & 7)) & 7) << 4));
-                        const float4 a0 = *(const float4 *)(v0 + ch * 8), a1 = *(const float4 *)(v0 + ch * 8 + 4);
-                        const float4 b0 = *(const float4 *)(v1 + ch * 8), b1 = *(const float4 *)(v1 + ch * 8 + 4);
-                        const uint32_t wq[4] = {q.x, q.y, q.z, q.w};
-                        const float va[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-                        const float vb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                        for (int e2 = 0; e2 < 4; ++e2) {
-                            // |w| of the pair as floats (bf16 bits in the high half)
-                            const float wlo = __uint_as_float((wq[e2] & 0x7fffu) << 16);
-                            const float whi = __uint_as_float(wq[e2] & 0x7fff0000u);
-                            xa0 = ru_fma(wlo, va[2 * e2], xa0);
-                            xa1 = ru_fma(whi, va[2 * e2 + 1], xa1);
-                            xb0 = ru_fma(wlo, vb[2 * e2], xb0);
-                            xb1 = ru_fma(whi, vb[2 * e2 + 1], xb1);
-                        }
-                    }
-                }
-                __syncwarp();
-                if (x.lane == 0) ptx::mbar_arrive(&x.bars[2 + st]);
-                if (tid == PRODUCER) issue_upto(g0 + (uint32_t)s + 3);
             }
-            gring = g0 + Lt::S;
+            gring = g0 + Lt::S * Lt::UPS;
             if (!ptx::mbar_wait(&x.bars[4], accn & 1u, spins)) fail(x, p, 5);
             accn++;
-            if (tid == PRODUCER) issue_upto(gring + 2);  // next layer's (or tile's) first slices, during the epilogue
-            // the other group's box: hand over this thread's half of its |W_b| v
-            float *xp = (float *)(x.smem + Lt::XP_OFF);
-            const float xown = ru_add(g == 0 ? xa0 : xb0, g == 0 ? xa1 : xb1);
-            xp[(1 - g) * H + i] = ru_add(g == 0 ? xb0 : xa0, g == 0 ? xb1 : xa1);
+            if (tid == PRODUCER) issue_upto(gring + 2);  // next layer's (or tile's) first units, during the epilogue
+            float xown;
+            if constexpr (NB == 2) {
+                // the other group's box: hand over this thread's half of its |W_b| v
+                float *xp = (float *)(x.smem + Lt::XP_OFF);
+                xown = ru_add(g == 0 ? xa0 : xb0, g == 0 ? xa1 : xb1);
+                xp[(1 - g) * H + i] = ru_add(g == 0 ? xb0 : xa0, g == 0 ? xb1 : xa1);
+            } else {
+                xown = ru_add(xa0, xa1);
+            }
             ptx::tc_fence_after();
             if (__syncthreads_or(*x.abort_flag != 0)) break;  // every operand read of this layer is done
             // ---- epilogue of the group's box -------------------------------
-            const float xacc = ru_add(xown, xp[g * H + i]);
+            const float xacc = NB == 2 ? ru_add(xown, ((const float *)(x.smem + Lt::XP_OFF))[g * H + i]) : xown;
             hidden_epilogue<H, SOUND, ACT>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
-                                      tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
+                                           tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
         }
         if (__syncthreads_or(*x.abort_flag != 0)) break;
         // ---- output layer (H -> 1) on the SIMT cores ------------------------------
@@ -1026,7 +1076,12 @@ __global__ void __launch_bounds__(2 * H, 1) tc_bound_kernel(const __grid_constan
 }  // namespace tc
 
 int tc_smem_bytes(int H) {
-    return H == 256 ? tc::Layout<256>::ALLOC : (H == 128 ? tc::Layout<128>::ALLOC : 0);
+    return H == 512 ? tc::Layout<512>::ALLOC
+                    : (H == 256 ? tc::Layout<256>::ALLOC : (H == 128 ? tc::Layout<128>::ALLOC : 0));
+}
+
+int tc_boxes_per_tile(int H) {
+    return H == 512 ? tc::Layout<512>::NB : (H == 256 ? tc::Layout<256>::NB : tc::Layout<128>::NB);
 }
 
 template <int H, bool SOUND, int ACT>
@@ -1035,7 +1090,7 @@ static cudaError_t launch_one(const TcParams &p, const BoxSrc &src, const BoundO
     cudaError_t e =
         cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND, ACT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc::tc_bound_kernel<H, SOUND, ACT><<<grid, 2 * H, smem, st>>>(p, src, out);
+    tc::tc_bound_kernel<H, SOUND, ACT><<<grid, tc::Layout<H>::NT, smem, st>>>(p, src, out);
     return cudaGetLastError();
 }
 
@@ -1058,6 +1113,7 @@ static cudaError_t launch_h(bool sound, const TcParams &p, const BoxSrc &src, co
 
 cudaError_t launch_tc_bound(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
                             cudaStream_t st) {
+    if (H == 512) return launch_h<512>(sound, p, src, out, grid, st);
     if (H == 256) return launch_h<256>(sound, p, src, out, grid, st);
     if (H == 128) return launch_h<128>(sound, p, src, out, grid, st);
     return cudaErrorInvalidValue;

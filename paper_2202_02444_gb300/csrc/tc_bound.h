@@ -28,6 +28,7 @@ struct TcParams {
 };
 
 int tc_smem_bytes(int H);
+int tc_boxes_per_tile(int H);  // boxes one CTA bounds at a time
 cudaError_t launch_tc_bound(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
                             cudaStream_t st);
 

@@ -135,6 +135,8 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
         (wl.make_mlp([128] * 3, "elu", seed=35), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 640, 7),
         (wl.make_mlp([256] * 3, "sin", seed=39), dict(arith="truncate", K=64, precision="bf16_sound"), 6, 513, 9),
         (wl.make_mlp([128] * 4, "sin", seed=41), dict(arith="truncate", K=64, precision="bf16"), 5, 300, 8),
+        (wl.make_mlp([512] * 3, "relu", seed=42), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 301, 7),
+        (wl.make_mlp([512] * 4, "elu", seed=47), dict(arith="truncate", K=64, precision="bf16"), 3, 64, 6),
     ]
     nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
     try:

@@ -47,7 +47,10 @@ NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 
         "elu128x4": lambda: wl.make_mlp([128] * 4, "elu", seed=35),
         "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37),
         "sin128x4": lambda: wl.make_mlp([128] * 4, "sin", seed=41),
-        "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39)}
+        "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39),
+        "relu512x4": lambda: wl.make_mlp([512] * 4, "relu", seed=43),
+        "elu512x3": lambda: wl.make_mlp([512] * 3, "elu", seed=44),
+        "sin512x3": lambda: wl.make_mlp([512] * 3, "sin", seed=45)}
 
 
 @pytest.mark.parametrize("name", list(NETS))
@@ -98,7 +101,9 @@ SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
            "elu128x3": lambda: wl.make_mlp([128] * 3, "elu", seed=36),
            "elu256x3": lambda: wl.make_mlp([256] * 3, "elu", seed=37),
            "sin128x3": lambda: wl.make_mlp([128] * 3, "sin", seed=38),
-           "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39)}
+           "sin256x3": lambda: wl.make_mlp([256] * 3, "sin", seed=39),
+           "relu512x3": lambda: wl.make_mlp([512] * 3, "relu", seed=46),
+           "elu512x3": lambda: wl.make_mlp([512] * 3, "elu", seed=44)}
 # box half-widths: the SIREN nets (omega0 = 30 folded into the weights) need
 # smaller boxes before the oracle decides a sizeable share of them
 SHALLOW_BOXES = {"sin128x3": (1 / 1024, 1 / 128), "sin256x3": (1 / 4096, 1 / 256)}
@@ -122,7 +127,8 @@ def test_bf16_sound_classes_on_shallow_nets(sra, name):
     mlp = SHALLOW[name]()
     net = sra.Net(mlp)
     hw_lo, hw_hi = SHALLOW_BOXES.get(name, (1 / 256, 1 / 16))
-    c, h = wl.make_boxes(1021, seed=7, hw_lo=hw_lo, hw_hi=hw_hi)
+    H = mlp.widths[1]
+    c, h = wl.make_boxes(1021 if H < 512 else 255, seed=7, hw_lo=hw_lo, hw_hi=hw_hi)
     lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
     ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
     tie = ref["sel_gap"] < 1e-2
@@ -130,9 +136,9 @@ def test_bf16_sound_classes_on_shallow_nets(sra, name):
     slack = 1e-6 * scale
     assert np.all(((lo <= ref["lo"] + slack) & (hi >= ref["hi"] - slack)) | tie)
     assert not np.any(((cls == 1) & (ref["cls"] == 2)) | ((cls == 2) & (ref["cls"] == 1)))
-    H = mlp.widths[1]
     u = (2.0 ** -16 + 17 * (2 * H // 16) * 2.0 ** -23 * (1 + 2.0 ** -7)) * 1.001
-    mcls = emulate(mlp, c, h, 64, "xinf", u, u_store=2.0 ** -8, u_first=2.0 ** -22)[0]
+    mcls = np.concatenate([emulate(mlp, c[k:k + 128], h[k:k + 128], 64, "xinf", u, u_store=2.0 ** -8,
+                                   u_first=2.0 ** -22)[0] for k in range(0, len(c), 128)])
     dec = ref["cls"] != 0
     lost, lost_model = dec & (cls == 0), dec & (mcls == 0)
     print(f"{name}: oracle UNKNOWN {np.mean(~dec):.4f}, BF16-sound UNKNOWN {np.mean(cls == 0):.4f} "
@@ -181,7 +187,7 @@ def test_bf16_unsupported_shapes(sra):
     net.close()
 
 
-@pytest.mark.parametrize("name", ["relu256x8", "elu256x3", "sin256x3"])
+@pytest.mark.parametrize("name", ["relu256x8", "elu256x3", "sin256x3", "relu512x4", "elu512x3"])
 def test_bf16_plain_tracks_oracle(sra, name):
     """Plain BF16 tensor-core bounds (no rounding radius): error against the
     FP64 oracle is stated per box; it comes from the BF16 rounding of the
