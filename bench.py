@@ -68,7 +68,7 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true,ReLU>": {"sha1": "d34369b92373d669c08e8105f2f146009620f713", "bytes": 3014912,
+    "tc_bound_kernel<256,true,ReLU>": {"sha1": "159c2ae04442d667458914fe85570a15f8190a4b", "bytes": 2996736,
                                        "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
@@ -117,7 +117,7 @@ def parse_args():
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16", "full_fp32"],
+                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16", "full_fp32", "bf16_sound_512"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
     ap.add_argument("--serve-rates", default="2,4,8,16", help="request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
@@ -585,7 +585,8 @@ def kernel_case(args):
     """The dominant kernel alone, for profilers: two sra_bound_boxes calls on
     --batch boxes (half-widths log-uniform in [1/1024, 1/64]) of the
     3-[256]x8-1 ReLU net, affine-truncate K=64 in the given precision, or
-    affine-full in FP32 (full_fp32)."""
+    affine-full in FP32 (full_fp32), or BF16-sound on the 3-[512]x4-1 ReLU
+    net (bf16_sound_512)."""
     import torch
     from paper_2202_02444_gb300 import sra
     if args.kernel_case in ("rays", "rays_bf16"):  # central camera rays, 300-iteration cap
@@ -602,11 +603,14 @@ def kernel_case(args):
         torch.cuda.synchronize()
         print("kernel case done rays")
         return
-    net = sra.Net(wl.net_relu256x8())
+    wide = args.kernel_case == "bf16_sound_512"  # the width-512 net of policies.tc_widths
+    net = sra.Net(wl.make_mlp([512] * 4, "relu", seed=51) if wide else wl.net_relu256x8())
     c, h = wl.make_boxes(args.batch, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
     C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
     if args.kernel_case == "full_fp32":  # affine-full, the noise matrix in device memory
         o = sra.make_opts(arith="full")
+    elif wide:
+        o = sra.make_opts(arith="truncate", K=64, precision="bf16_sound")
     else:
         o = sra.make_opts(arith="truncate", K=64, precision=args.kernel_case)
     for _ in range(2):
