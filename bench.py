@@ -71,8 +71,8 @@ TRAFFIC = {
     "tc_bound_kernel<256,true,ReLU>": {"sha1": "159c2ae04442d667458914fe85570a15f8190a4b", "bytes": 2996736,
                                        "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
-TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
-                    "paper_2202_02444_gb300/csrc/tc_bound.h")
+TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_bound_impl.cuh",
+                    "paper_2202_02444_gb300/csrc/tc_ptx.cuh", "paper_2202_02444_gb300/csrc/tc_bound.h")
 
 
 def sources_sha1(paths):
@@ -321,10 +321,14 @@ def batched_phase(sra, torch, cap):
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
     # the same 64 trees with BF16-sound bounds on the tensor cores for every
-    # network that has that kernel (one width 128, 256 or 512, K = 64), the
-    # others in their autotuned FP32 form, all in the same batched rounds
+    # network that has that kernel (one width 128, 256 or 512; K = 16, 32 or
+    # 64), the others in their autotuned FP32 form, all in the same batched
+    # rounds
     tc = [tc_box_net(m) for m in mlps]
-    opts_tc = [sra.make_opts(arith="truncate", K=64, precision="bf16_sound") if t else o for t, o in zip(tc, opts)]
+    # the tensor-core kernel's K: the autotuned one where it has a kernel for it (16, 32, 64), else 64
+    k_tc = [r["K"] if r["K"] in (16, 32, 64) else 64 for r in tuned]
+    opts_tc = [sra.make_opts(arith="truncate", K=kt, precision="bf16_sound") if t else o
+               for t, o, kt in zip(tc, opts, k_tc)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     res_tc, rounds_tc = batch.build_trees(nets, opts_tc, depths, cap=cap)
@@ -334,10 +338,15 @@ def batched_phase(sra, torch, cap):
         if t:
             sra.sync_status(n)
     nodes_tc = sum(r["nodes"] for r in res_tc)
-    flop_tc = sum(r["nodes"] * box_flops(m, 64 if t else u["K"]) for r, m, t, u in zip(res_tc, mlps, tc, tuned))
+    flop_tc = sum(r["nodes"] * box_flops(m, kt if t else u["K"]) for r, m, t, u, kt in zip(res_tc, mlps, tc, tuned, k_tc))
+    ks_tc = {}
+    for t, kt in zip(tc, k_tc):
+        if t:
+            ks_tc[str(kt)] = ks_tc.get(str(kt), 0) + 1
     bf16_sound = {"nets_on_tensor_cores": int(sum(tc)), "box_evals": nodes_tc, "rounds": rounds_tc, "s": t_tc,
                   "evals_per_s": nodes_tc / t_tc, "tflops": flop_tc / t_tc / 1e12,
                   "tensor_core_box_evals": int(sum(r["nodes"] for r, t in zip(res_tc, tc) if t)),
+                  "tensor_core_K": ks_tc,
                   "nets_truncated_at_cap": int(sum(r["truncated"] for r in res_tc)),
                   "tensor_core_nets_truncated_at_cap": int(sum(r["truncated"] for r, t in zip(res_tc, tc) if t))}
     for n in nets:
@@ -447,6 +456,16 @@ def tc_widths_phase(sra, torch, dev, timed):
             row[prec] = {"box_evals_per_s": B / (ms / 1e3), "tflops": tf,
                          "frac_of_bf16_peak": tf / peak if prec != "fp32" else None,
                          "unknown_frac": float((cl == 0).float().mean())}
+        if H == 256:  # the other kept-symbol counts of the kernel
+            row["bf16_sound_by_K"] = {}
+            for K in (16, 32):
+                o = sra.make_opts(arith="truncate", K=K, precision="bf16_sound")
+                ms, (lo, hi, cl) = timed(lambda: sra.bound_boxes(net, C_, H_, opts=o))
+                sra.sync_status(net)
+                fk = box_flops(mlp, K)
+                row["bf16_sound_by_K"][str(K)] = {"box_evals_per_s": B / (ms / 1e3), "flop_per_box": fk,
+                                                  "tflops": fk * B / (ms / 1e3) / 1e12,
+                                                  "frac_of_bf16_peak": fk * B / (ms / 1e3) / 1e12 / peak}
         out["widths"][str(H)] = row
         net.close()
     return out

@@ -82,7 +82,7 @@ enum { SRA_SLOPE_CHEBYSHEV = 0, SRA_SLOPE_MINRANGE = 1 };
  *               rounding of the noise columns).
  * BF16_SOUND and BF16 serve 3 -> H x L -> 1 networks whose hidden layers are
  * all ReLU, all ELU or all sin (H = 128, 256 or 512, up to 12 hidden layers) with
- * affine-truncate K = 64 and the Chebyshev slope; other shapes and options
+ * affine-truncate K = 16, 32 or 64 and the Chebyshev slope; other shapes and options
  * return SRA_EUNSUPPORTED. */
 enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2, SRA_PREC_BF16 = 3 };
 
@@ -231,7 +231,7 @@ typedef struct {
  * int64[n_segs][SRA_CNT_N], zeroed by the caller (or holding earlier
  * chunks' totals, which are appended after). Precision FP32 (the SIMT
  * launches above) or, for networks with the tensor-core path (3 -> H x L -> 1
- * ReLU, ELU or sin, H = 128, 256 or 512) and affine-truncate K = 64, SRA_PREC_BF16 /
+ * ReLU, ELU or sin, H = 128, 256 or 512) and affine-truncate K = 16, 32 or 64, SRA_PREC_BF16 /
  * SRA_PREC_BF16_SOUND: each such segment runs one tensor-core launch beside
  * the SIMT launches (check sra_sync_status on its network for a timed-out
  * wait). recheck and converge must be 0; FP64 is not batched; otherwise

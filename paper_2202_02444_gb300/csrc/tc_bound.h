@@ -29,7 +29,12 @@ struct TcParams {
 
 int tc_smem_bytes(int H);
 int tc_boxes_per_tile(int H);  // boxes one CTA bounds at a time
-cudaError_t launch_tc_bound(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid,
-                            cudaStream_t st);
+bool tc_kt_served(int K);      // kept-symbol counts with a kernel: 16, 32, 64
+// K kept noise symbols (16, 32 or 64), width H (128, 256 or 512)
+cudaError_t launch_tc_bound(int H, int K, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out,
+                            int grid, cudaStream_t st);
+template <int KT>
+cudaError_t launch_tc_bound_kt(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out,
+                               int grid, cudaStream_t st);
 
 }  // namespace sra

@@ -226,6 +226,36 @@ __device__ __forceinline__ void tmem_ld16x256_x8(uint32_t taddr, float *v) {
     for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_ld16x256_x2(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// JJ chunks of 8 columns (JJ = 2, 4 or 8) in the 16x256b layout: v[4 j + q]
+// is register q of chunk j.
+template <int JJ> __device__ __forceinline__ void tmem_ld16x256_chunks(uint32_t taddr, float *v) {
+    static_assert(JJ == 2 || JJ == 4 || JJ == 8, "chunks");
+    if constexpr (JJ == 8) tmem_ld16x256_x8(taddr, v);
+    else if constexpr (JJ == 4) tmem_ld16x256_x4(taddr, v);
+    else tmem_ld16x256_x2(taddr, v);
+}
+
 // Four 8x8 b16 matrices stored transposed: register r[m] of thread t holds
 // elements (row t/4, columns 2(t%4), 2(t%4)+1) of matrix m (low half first);
 // memory row k of matrix m (16 bytes at the address thread 8m + k supplies)

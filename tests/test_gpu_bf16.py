@@ -71,6 +71,40 @@ def test_bf16_sound_contains_samples(sra, name):
     net.close()
 
 
+KT_CASES = [("relu256x8", 16), ("relu256x8", 32), ("sin256x3", 16), ("elu128x4", 32), ("relu512x4", 16),
+            ("elu512x3", 32)]
+
+
+@pytest.mark.parametrize("name,K", KT_CASES)
+def test_bf16_kept_symbols(sra, name, K):
+    """The tensor-core kernel with K = 16 or 32 kept symbols (Sec. 3.3
+    truncate). BF16-sound: every sampled value of f lies inside [lo, hi]
+    (no tolerance) and the range contains the oracle's affine-truncate-K
+    range (selection near-ties exempt). Plain BF16: radius within 2 % of the
+    oracle's radius plus 1e-3 of its scale |c| + r (the BF16 operand
+    rounding of the noise columns is relative to the scale: a box whose
+    radius is small against |c| sees it as a larger relative radius error),
+    centre within 1e-3 of the scale."""
+    mlp = NETS[name]()
+    net = sra.Net(mlp)
+    c, h = level_boxes(255, seed=11)
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=K, precision="bf16_sound")
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=K)
+    tie = ref["sel_gap"] < 1e-2
+    assert np.all(((lo <= ref["lo"]) & (hi >= ref["hi"])) | tie)
+    for i in range(len(c)):
+        f = forward(mlp, box_samples(c[i], h[i], n_grid=3, n_rand=48, seed=i))
+        assert f.min() >= lo[i] and f.max() <= hi[i], (i, f.min(), f.max(), lo[i], hi[i])
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=K, precision="bf16")
+    scale = np.abs(ref["y0"]) + ref["rad"]
+    dc = np.abs(0.5 * (lo + hi) - ref["y0"]) / scale
+    dr = np.abs(0.5 * (hi - lo) - ref["rad"]) / ref["rad"]
+    print(f"{name} K={K}: plain centre err/scale max {dc.max():.2e}, radius rel err max {dr.max():.2e}")
+    assert np.all((np.abs(0.5 * (hi - lo) - ref["rad"]) < 2e-2 * ref["rad"] + 1e-3 * scale) | tie)
+    assert np.all((dc < 1e-3) | tie)
+    net.close()
+
+
 def test_bf16_vs_oracle_excess(sra):
     """Against the FP64 oracle: decided classes never contradict it and the
     oracle's center lies in the BF16-sound range. The radius excess is
@@ -109,8 +143,11 @@ SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
 SHALLOW_BOXES = {"sin128x3": (1 / 1024, 1 / 128), "sin256x3": (1 / 4096, 1 / 256)}
 
 
-@pytest.mark.parametrize("name", list(SHALLOW))
-def test_bf16_sound_classes_on_shallow_nets(sra, name):
+SHALLOW_K = {"relu256x3": 32, "elu128x3": 16}  # more kept-symbol counts than K = 64
+
+
+@pytest.mark.parametrize("name,K", [(n, 64) for n in SHALLOW] + list(SHALLOW_K.items()))
+def test_bf16_sound_classes_on_shallow_nets(sra, name, K):
     """Where the |W| amplification of the a-priori rounding radius is small
     (two tensor-core layers), the sound form decides nearly everything the
     oracle decides. Gates: the sound bound contains the oracle's (boxes whose
@@ -129,19 +166,19 @@ def test_bf16_sound_classes_on_shallow_nets(sra, name):
     hw_lo, hw_hi = SHALLOW_BOXES.get(name, (1 / 256, 1 / 16))
     H = mlp.widths[1]
     c, h = wl.make_boxes(1021 if H < 512 else 255, seed=7, hw_lo=hw_lo, hw_hi=hw_hi)
-    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=64, precision="bf16_sound")
-    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=64)
+    lo, hi, cls = run(sra, net, c, h, arith="truncate", K=K, precision="bf16_sound")
+    ref = oracle.bound_boxes(mlp, c, h, "truncate", K=K)
     tie = ref["sel_gap"] < 1e-2
     scale = np.abs(ref["y0"]) + ref["rad"]
     slack = 1e-6 * scale
     assert np.all(((lo <= ref["lo"] + slack) & (hi >= ref["hi"] - slack)) | tie)
     assert not np.any(((cls == 1) & (ref["cls"] == 2)) | ((cls == 2) & (ref["cls"] == 1)))
     u = (2.0 ** -16 + 17 * (2 * H // 16) * 2.0 ** -23 * (1 + 2.0 ** -7)) * 1.001
-    mcls = np.concatenate([emulate(mlp, c[k:k + 128], h[k:k + 128], 64, "xinf", u, u_store=2.0 ** -8,
+    mcls = np.concatenate([emulate(mlp, c[k:k + 128], h[k:k + 128], K, "xinf", u, u_store=2.0 ** -8,
                                    u_first=2.0 ** -22)[0] for k in range(0, len(c), 128)])
     dec = ref["cls"] != 0
     lost, lost_model = dec & (cls == 0), dec & (mcls == 0)
-    print(f"{name}: oracle UNKNOWN {np.mean(~dec):.4f}, BF16-sound UNKNOWN {np.mean(cls == 0):.4f} "
+    print(f"{name} K={K}: oracle UNKNOWN {np.mean(~dec):.4f}, BF16-sound UNKNOWN {np.mean(cls == 0):.4f} "
           f"(model {np.mean(mcls == 0):.4f}); decided by the oracle but not by BF16-sound {lost.sum()} "
           f"(model {lost_model.sum()}) of {dec.sum()}")
     assert lost.sum() <= lost_model.sum() + 0.01 * dec.sum()
@@ -176,6 +213,9 @@ def test_bf16_unsupported_shapes(sra):
     assert e.value.code == sra.EUNSUPPORTED
     with pytest.raises(sra.SraError) as e:  # the kernel's rules use the Chebyshev slope
         sra.bound_boxes(net, c, c, arith="truncate", K=64, slope="minrange", precision="bf16_sound")
+    assert e.value.code == sra.EUNSUPPORTED
+    with pytest.raises(sra.SraError) as e:  # kernels for K = 16, 32 and 64 only
+        sra.bound_boxes(net, c, c, arith="truncate", K=48, precision="bf16")
     assert e.value.code == sra.EUNSUPPORTED
     net.close()
     mixed = wl.make_mlp([128] * 3, "relu", seed=2)
