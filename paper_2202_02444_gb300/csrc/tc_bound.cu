@@ -40,11 +40,13 @@ extern template cudaError_t launch_tc_bound_kt<16>(int, bool, const TcParams &, 
                                                    int, cudaStream_t);
 
 int tc_smem_bytes(int H) {
-    return H == 512 ? tc::Layout<512, 64>::ALLOC
-                    : (H == 256 ? tc::Layout<256, 64>::ALLOC : (H == 128 ? tc::Layout<128, 64>::ALLOC : 0));
+    return H == 512   ? tc::Layout<512, 64, tc::boxes_per_tile(512)>::ALLOC
+           : H == 256 ? tc::Layout<256, 64, tc::boxes_per_tile(256)>::ALLOC
+           : H == 128 ? tc::Layout<128, 64, tc::boxes_per_tile(128)>::ALLOC
+                      : 0;
 }
 
-int tc_boxes_per_tile(int H) { return H == 512 ? tc::Layout<512, 64>::NB : tc::Layout<256, 64>::NB; }
+int tc_boxes_per_tile(int H) { return tc::boxes_per_tile(H); }
 
 bool tc_kt_served(int K) { return K == 16 || K == 32 || K == 64; }
 

@@ -17,16 +17,21 @@ constexpr int NCC = 16;      // center-chunk columns (MMA N)
 constexpr int NPART = 4;     // partial sums per output-layer dot product
 constexpr uint32_t kSpin = 1u << 22;
 
-template <int H, int KT> struct Layout {
+// Boxes per tile (one thread group of H threads each) for width H: two at
+// H = 128 and 256, one at H = 512 (two would need 576 TMEM columns).
+constexpr int boxes_per_tile(int H) { return H == 512 ? 1 : 2; }
+
+template <int H, int KT, int NBV> struct Layout {
     // KT kept noise symbols per box (16, 32 or 64)
-    static constexpr int NB = H == 512 ? 1 : 2;  // boxes per tile (one thread group each)
+    static constexpr int NB = NBV;               // boxes per tile (one thread group each)
     static constexpr int NT = NB * H;            // threads per CTA
     static constexpr int NA = NB * KT;           // noise columns per tile
     static constexpr int MT = H / 128;   // M tiles per layer
     static constexpr int S = H / 64;     // K slices per layer
     // TMEM columns per M tile: NA noise then NCC center accumulators
-    static constexpr int TM_STRIDE = H == 512 ? 128 : 256;
-    static constexpr int UPS = H == 512 ? 2 : 1;  // ring units per K slice
+    static constexpr int TM_STRIDE = NB == 1 ? 128 : 256;
+    static constexpr int TMEM_COLS = MT * TM_STRIDE <= 256 ? 256 : 512;  // allocated (a power of two)
+    static constexpr int UPS = NB == 1 ? 2 : 1;  // ring units per K slice
     static constexpr int MPU = MT / UPS;          // M tiles per ring unit
     static constexpr int TILE = 128 * 128;                  // bytes of one 128 x 64 bf16 tile
     static constexpr int STAGE = 2 * MPU * TILE;            // W_b and W_r tiles of one unit
@@ -46,17 +51,18 @@ template <int H, int KT> struct Layout {
     static constexpr int OUT_OFF = PART_OFF + NB * (H / 32) * KT * 4;  // Y,E [NB][NPART][KT+2]
     static constexpr int WOUT_OFF = OUT_OFF + 2 * NB * NPART * (KT + 2) * 4;  // wout[H]
     static constexpr int BOX_OFF = WOUT_OFF + H * 4;                 // box c/h [NB][8]
-    static constexpr int XP_OFF = BOX_OFF + NB * 8 * 4;              // |W_b| v partials [NB][H]
+    static constexpr int XP_OFF = BOX_OFF + NB * 8 * 4;              // |W_b| v partials [NB][H] (two boxes)
     static constexpr int NCH = (KT + H + 31) / 32;                    // candidate chunks of 32
     static constexpr int KMW = NCH <= 16 ? 16 : 32;                  // kept-mask words per box
-    static constexpr int KM_OFF = XP_OFF + NB * H * 4;               // kept masks [NB][KMW]
+    static constexpr int KM_OFF = XP_OFF + (NB == 2 ? NB * H * 4 : 0);  // kept masks [NB][KMW]
     static constexpr int NEW_OFF = KM_OFF + NB * KMW * 4;            // newlist[NB][KT]
     static constexpr int BAR_OFF = ((NEW_OFF + NB * KT * 4) + 15) & ~15;   // 5 mbarriers
     static constexpr int MISC_OFF = BAR_OFF + 64;  // tmem slot, abort, nnew[NB], sel[NB][2]
     static constexpr int DUMMY_OFF = MISC_OFF + 64;  // 32 x 16 B sink for dropped columns' stores
     static constexpr int BYTES = DUMMY_OFF + 512;
     static constexpr int ALLOC = BYTES + 1024;     // + alignment slack
-    static_assert(MPU * UPS == MT && NA + NCC <= TM_STRIDE && MT * TM_STRIDE <= 512, "TMEM columns");
+    static_assert(MPU >= 1 && MPU * UPS == MT && NA + NCC <= TM_STRIDE && MT * TM_STRIDE <= TMEM_COLS,
+                  "TMEM columns");
     static_assert(NCH <= KMW && NB <= 2, "kept masks");
     static_assert(XA_OFF % 1024 == 0 && XA_SLICE % 1024 == 0 && XC_OFF % 1024 == 0, "operand alignment");
     static_assert(ALLOC <= 232448, "shared memory");
@@ -310,9 +316,9 @@ __device__ __forceinline__ float operand_mag_bound(float al, float sa, float ga)
 // mask of every chunk of 32 candidates, the kept new symbols newlist[q] =
 // position | neuron << 16 and nnew to shared memory, valid after the
 // caller's next group_sync.
-template <int H, int KT>
+template <int H, int KT, int NBV>
 __device__ void select_topk(const Ctx &x, int Ncur) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     constexpr int NW = H / 32, NCH = Lt::NCH;
     if (x.wg != x.g) return;  // warps 0 and H/32 + 1: different schedulers
     const int g = x.g, lane = x.lane;
@@ -397,8 +403,8 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
 }
 
 // Kept flag of candidate c of the group's box (after select_topk and a group_sync).
-template <int H, int KT> __device__ __forceinline__ bool cand_kept(const Ctx &x, int c) {
-    using Lt = Layout<H, KT>;
+template <int H, int KT, int NBV> __device__ __forceinline__ bool cand_kept(const Ctx &x, int c) {
+    using Lt = Layout<H, KT, NBV>;
     const uint32_t *km = (const uint32_t *)(x.smem + Lt::KM_OFF) + x.g * Lt::KMW;
     return (km[c >> 5] >> (c & 31)) & 1u;
 }
@@ -407,9 +413,9 @@ template <int H, int KT> __device__ __forceinline__ bool cand_kept(const Ctx &x,
 // group's box): one-hot columns, the neuron's magnitude ga (read back from
 // the candidate scores) at its own entry and zeros elsewhere, written as
 // 16-byte chunks of eight neurons.
-template <int H, bool SOUND, int KT>
+template <int H, bool SOUND, int KT, int NBV>
 __device__ __forceinline__ void fill_new_rows(const Ctx &x, int Ncur) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     const int g = x.g, i = x.i;
     const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     const int *newlist = (const int *)(x.smem + Lt::NEW_OFF) + g * KT;
@@ -440,9 +446,9 @@ __device__ __forceinline__ void fill_new_rows(const Ctx &x, int Ncur) {
 // Center (as a BF16 hi/lo pair, operand chunk XC), independent part and the
 // sound operand vector v = rho1 |operand| + x_r of neuron n of the group's
 // box, for the next layer's MMA and |W_b| v pass.
-template <int H, bool SOUND, int KT>
+template <int H, bool SOUND, int KT, int NBV>
 __device__ __forceinline__ void store_neuron(const Ctx &x, const TcParams &p, int n, float c2, float xi, float mag) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     const int g = x.g;
     const uint32_t kk = (uint32_t)(n & 63);
     const __nv_bfloat16 chi = __float2bfloat16_rn(c2);
@@ -465,10 +471,10 @@ __device__ __forceinline__ void store_neuron(const Ctx &x, const TcParams &p, in
 // First layer (3 -> H, SIMT): thread i holds neuron i's three noise entries
 // a0 (already scaled by its slope al); truncation over 3 old + H new
 // candidates; operand rows written element-wise.
-template <int H, bool SOUND, int KT>
+template <int H, bool SOUND, int KT, int NBV>
 __device__ void first_layer_store(const Ctx &x, const TcParams &p, const float (&a0)[3], float sa, float al,
                                   float ga, float c2, float xi) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     const int g = x.g, i = x.i, lane = x.lane, wg = x.wg;
     float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
@@ -479,7 +485,7 @@ __device__ void first_layer_store(const Ctx &x, const TcParams &p, const float (
     }
     score[3 + i] = ga;
     group_sync(g, H);
-    select_topk<H, KT>(x, 3);
+    select_topk<H, KT, NBV>(x, 3);
     group_sync(g, H);
     const uint32_t km0 = ((const uint32_t *)(x.smem + Lt::KM_OFF))[g * Lt::KMW];
     unsigned char *XA = x.smem + Lt::XA_OFF + (i >> 6) * Lt::XA_SLICE;
@@ -494,9 +500,9 @@ __device__ void first_layer_store(const Ctx &x, const TcParams &p, const float (
             *(__nv_bfloat16 *)(XA + ptx::sw128_offset((uint32_t)(g * KT + pp), kk)) = __float2bfloat16_rn(a0[k]);
         }
     }
-    if (!cand_kept<H, KT>(x, 3 + i)) dropped = ru_add(dropped, ga);
-    fill_new_rows<H, SOUND, KT>(x, 3);
-    store_neuron<H, SOUND, KT>(x, p, i, c2, ru_add(xi, dropped), SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
+    if (!cand_kept<H, KT, NBV>(x, 3 + i)) dropped = ru_add(dropped, ga);
+    fill_new_rows<H, SOUND, KT, NBV>(x, 3);
+    store_neuron<H, SOUND, KT, NBV>(x, p, i, c2, ru_add(xi, dropped), SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
 }
 
 // Sum of N (a power of two) non-negative values, rounded up, as a balanced tree.
@@ -535,10 +541,10 @@ __device__ __forceinline__ float quad_scatter_ru(const float (&v)[4], int q) {
 //
 // Thread i's own neuron enters as its two center accumulators (TMEM columns
 // ccol, ccol + 1 of its lane), its bias and its |W_b| v sum xacc.
-template <int H, bool SOUND, int ACT, int KT>
+template <int H, bool SOUND, int ACT, int KT, int NBV>
 __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, int col0, uint32_t ccol, float bias,
                                 float xacc) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     const int g = x.g, lane = x.lane, wg = x.wg;
     float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
@@ -638,7 +644,7 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
         }
     }
     group_sync(g, H);
-    select_topk<H, KT>(x, KT);
+    select_topk<H, KT, NBV>(x, KT);
     group_sync(g, H);
     const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * Lt::KMW;
     // kept flags of the KT old columns (candidates 0 .. KT-1; the bits above
@@ -696,15 +702,15 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
             ptx::stmatrix_x4_trans(addr, R[0], R[1], R[2], R[3]);
         }
     }
-    if (!cand_kept<H, KT>(x, KT + nq)) xi = ru_add(xi, ga);
-    fill_new_rows<H, SOUND, KT>(x, KT);
-    store_neuron<H, SOUND, KT>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
+    if (!cand_kept<H, KT, NBV>(x, KT + nq)) xi = ru_add(xi, ga);
+    fill_new_rows<H, SOUND, KT, NBV>(x, KT);
+    store_neuron<H, SOUND, KT, NBV>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
 }
 
-template <int H, bool SOUND, int ACT, int KT>
-__global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
+template <int H, bool SOUND, int ACT, int KT, int NBV>
+__global__ void __launch_bounds__(Layout<H, KT, NBV>::NT, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
                                                                     BoundOut out) {
-    using Lt = Layout<H, KT>;
+    using Lt = Layout<H, KT, NBV>;
     constexpr int NT = Lt::NT, NB = Lt::NB, NA = Lt::NA, TM_STRIDE = Lt::TM_STRIDE;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     Ctx x;
@@ -746,7 +752,7 @@ __global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __
         ((uint32_t *)(x.smem + Lt::XC_OFF + (e / (NCC * 32)) * Lt::XC_SLICE))[e % (NCC * 32)] = 0u;
     float *wout = (float *)(x.smem + Lt::WOUT_OFF);
     for (int e = tid; e < H; e += NT) wout[e] = p.wout[e];
-    if (warp == 0) ptx::tmem_alloc(tmem_slot, 512);
+    if (warp == 0) ptx::tmem_alloc(tmem_slot, Lt::TMEM_COLS);
     __syncthreads();
     ptx::tc_fence_after();
     x.tmem = *tmem_slot;
@@ -843,7 +849,7 @@ __global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __
             act_rule<SOUND, ACT>(am, c, xinf, p.ub2u, al, ga, c2, xi);
 #pragma unroll
             for (int d = 0; d < 3; ++d) a0[d] *= al;
-            first_layer_store<H, SOUND, KT>(x, p, a0, am, al, ga, c2, xi);
+            first_layer_store<H, SOUND, KT, NBV>(x, p, a0, am, al, ga, c2, xi);
         }
         // ---- hidden layers on the tensor cores ---------------------------------
         for (int l = 1; l + 1 < p.L; ++l) {
@@ -957,7 +963,7 @@ __global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __
             if (__syncthreads_or(*x.abort_flag != 0)) break;  // every operand read of this layer is done
             // ---- epilogue of the group's box -------------------------------
             const float xacc = NB == 2 ? ru_add(xown, ((const float *)(x.smem + Lt::XP_OFF))[g * H + i]) : xown;
-            hidden_epilogue<H, SOUND, ACT, KT>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
+            hidden_epilogue<H, SOUND, ACT, KT, NBV>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
                                            tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
         }
         if (__syncthreads_or(*x.abort_flag != 0)) break;
@@ -1076,7 +1082,7 @@ __global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __
     // leave: no MMA may still be writing TMEM; then free it
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 0) ptx::tmem_dealloc(x.tmem, 512);
+    if (warp == 0) ptx::tmem_dealloc(x.tmem, Lt::TMEM_COLS);
 }
 
 }  // namespace tc
@@ -1085,11 +1091,13 @@ __global__ void __launch_bounds__(Layout<H, KT>::NT, 1) tc_bound_kernel(const __
 // form and the activation rule for one kept-symbol count KT.
 template <int H, bool SOUND, int ACT, int KT>
 static cudaError_t launch_one(const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid, cudaStream_t st) {
-    const int smem = tc::Layout<H, KT>::ALLOC;
-    cudaError_t e = cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND, ACT, KT>,
+    constexpr int NBV = tc::boxes_per_tile(H);
+    using Lt = tc::Layout<H, KT, NBV>;
+    const int smem = Lt::ALLOC;
+    cudaError_t e = cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND, ACT, KT, NBV>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tc::tc_bound_kernel<H, SOUND, ACT, KT><<<grid, tc::Layout<H, KT>::NT, smem, st>>>(p, src, out);
+    tc::tc_bound_kernel<H, SOUND, ACT, KT, NBV><<<grid, Lt::NT, smem, st>>>(p, src, out);
     return cudaGetLastError();
 }
 
