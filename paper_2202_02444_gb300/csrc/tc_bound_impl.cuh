@@ -320,7 +320,7 @@ template <int H, int KT, int NBV>
 __device__ void select_topk(const Ctx &x, int Ncur) {
     using Lt = Layout<H, KT, NBV>;
     constexpr int NW = H / 32, NCH = Lt::NCH;
-    if (x.wg != x.g) return;  // warps 0 and H/32 + 1: different schedulers
+    if (x.wg != x.g) return;  // warp g of group g (with two groups warps 0 and H/32 + 1: different schedulers)
     const int g = x.g, lane = x.lane;
     const float *score = (const float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
     const float *part = (const float *)(x.smem + Lt::PART_OFF) + g * NW * KT;
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(Layout<H, KT, NBV>::NT, 1) tc_bound_kernel(con
                 }
             }
             group_sync(g, H);
-            // final sums by warp g of the group (warps 0 and H/32 + 1), two noise
+            // final sums by warp g of the group (with two groups warps 0 and H/32 + 1), two noise
             // columns per lane; the radius and error sums are rounded up in
             // any order, and the FP32 error factors gam_out / gam_c_out bound
             // sequential summation, hence every other order too
