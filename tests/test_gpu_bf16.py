@@ -105,6 +105,30 @@ def test_bf16_kept_symbols(sra, name, K):
     net.close()
 
 
+EDGE_NETS = {"relu128x4": NETS["relu128x4"], "relu256x8": NETS["relu256x8"], "relu512x4": NETS["relu512x4"]}
+
+
+@pytest.mark.parametrize("name", list(EDGE_NETS))
+@pytest.mark.parametrize("precision", ["bf16_sound", "bf16"])
+def test_bf16_batch_sizes(sra, name, precision):
+    """Ragged and degenerate batch sizes around the tile (two boxes at H <=
+    256, one at H = 512) and the persistent grid (one CTA per SM): a batch of
+    n boxes gives, bit for bit, what the first n boxes of a 400-box batch
+    give (a box's result depends only on its own data and its slot in the
+    tile, and the slots of the first n boxes are the same in both); n = 0
+    queues nothing."""
+    mlp = EDGE_NETS[name]()
+    net = sra.Net(mlp)
+    c, h = level_boxes(400, seed=13)
+    big = run(sra, net, c, h, arith="truncate", K=64, precision=precision)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for n in sorted({0, 1, 2, 3, sms - 1, sms, sms + 1, 2 * sms + 1, 399}):
+        small = run(sra, net, c[:n], h[:n], arith="truncate", K=64, precision=precision)
+        for a, b in zip(small, big):
+            assert np.array_equal(a, b[:n]), (name, n)
+    net.close()
+
+
 def test_bf16_vs_oracle_excess(sra):
     """Against the FP64 oracle: decided classes never contradict it and the
     oracle's center lies in the BF16-sound range. The radius excess is
