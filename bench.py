@@ -117,7 +117,8 @@ def parse_args():
     ap.add_argument("--precision", default="bf16_sound", choices=["fp32", "bf16", "bf16_sound"])
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--kernel-case", default=None,
-                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16", "full_fp32", "bf16_sound_512"],
+                    choices=["fp32", "bf16_sound", "bf16", "fp64", "rays", "rays_bf16", "full_fp32", "bf16_sound_512",
+                             "bf16_sound_k16"],
                     help="run only the bound kernel on --batch boxes of the 256x8 net twice (profiling)")
     ap.add_argument("--serve-rates", default="2,4,8,16", help="request rates (req/s) of the serving sweep")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving trace")
@@ -605,7 +606,8 @@ def kernel_case(args):
     --batch boxes (half-widths log-uniform in [1/1024, 1/64]) of the
     3-[256]x8-1 ReLU net, affine-truncate K=64 in the given precision, or
     affine-full in FP32 (full_fp32), or BF16-sound on the 3-[512]x4-1 ReLU
-    net (bf16_sound_512)."""
+    net (bf16_sound_512), or BF16-sound with K=16 on the 3-[256]x4-1 ReLU net
+    (bf16_sound_k16)."""
     import torch
     from paper_2202_02444_gb300 import sra
     if args.kernel_case in ("rays", "rays_bf16"):  # central camera rays, 300-iteration cap
@@ -623,13 +625,14 @@ def kernel_case(args):
         print("kernel case done rays")
         return
     wide = args.kernel_case == "bf16_sound_512"  # the width-512 net of policies.tc_widths
-    net = sra.Net(wl.make_mlp([512] * 4, "relu", seed=51) if wide else wl.net_relu256x8())
+    k16 = args.kernel_case == "bf16_sound_k16"  # the width-256 net of policies.tc_widths at K = 16
+    net = sra.Net(wl.make_mlp([512 if wide else 256] * 4, "relu", seed=51) if (wide or k16) else wl.net_relu256x8())
     c, h = wl.make_boxes(args.batch, seed=1, hw_lo=1 / 1024, hw_hi=1 / 64)
     C_, H_ = torch.from_numpy(c).cuda(), torch.from_numpy(h).cuda()
     if args.kernel_case == "full_fp32":  # affine-full, the noise matrix in device memory
         o = sra.make_opts(arith="full")
-    elif wide:
-        o = sra.make_opts(arith="truncate", K=64, precision="bf16_sound")
+    elif wide or k16:
+        o = sra.make_opts(arith="truncate", K=16 if k16 else 64, precision="bf16_sound")
     else:
         o = sra.make_opts(arith="truncate", K=64, precision=args.kernel_case)
     for _ in range(2):
