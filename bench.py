@@ -790,13 +790,15 @@ def main():
         d2h_list.append(cnt_host.numel() * 8 + nch * 8)
 
     # ray phase (separate from the step): a camera tile with an iteration cap,
-    # in each form: FP32 on the SIMT cores, split-BF16 hidden layers on tcgen05,
-    # and the latter with the FP64 re-check of rays that met a near-zero decision
+    # in each form: FP32 on the SIMT cores, split-BF16 hidden layers on tcgen05
+    # (plain, and BF16-sound: segment bounds with the a-priori rounding
+    # radius), and the BF16 forms with the FP64 re-check of rays that met a
+    # near-zero decision
     ray_forms, ray_t = {}, {}
     it_flop = ray_iter_flops(mlp_ray)
     rechecked = torch.zeros(1, dtype=torch.int64, device=dev)
-    for form in ("fp32", "bf16", "bf16_fp64_recheck"):
-        prec = "bf16" if form.startswith("bf16") else form
+    for form in ("fp32", "bf16", "bf16_fp64_recheck", "bf16_sound", "bf16_sound_fp64_recheck"):
+        prec = form.replace("_fp64_recheck", "")
         ropts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_iters,
                               precision=prec, recheck=form.endswith("recheck"), recheck_band=1e-5,
                               recheck_count=rechecked)
@@ -835,7 +837,7 @@ def main():
         slots = 16 * torch.cuda.get_device_properties(dev).multi_processor_count
         cro, crd = torch.from_numpy(o[csel]).to(dev), torch.from_numpy(d[csel]).to(dev)
         copts = sra.make_opts(arith="fixed", delta=1e-4, t_max=10.0, max_iters=args.ray_complete_cap,
-                              precision="bf16")
+                              precision="bf16_sound")
         tc_ = torch.empty(nc, dtype=torch.float32, device=dev)
         ic_ = torch.empty(nc, dtype=torch.int32, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -848,7 +850,7 @@ def main():
         t_c, i_c = tc_.cpu().numpy(), ic_.cpu().numpy()
         ended = ~np.isnan(t_c)
         it_mean = float(i_c[ended].mean()) if ended.any() else float("nan")
-        completion = {"rays": int(nc), "waves": nc / slots, "form": "bf16", "cap": args.ray_complete_cap,
+        completion = {"rays": int(nc), "waves": nc / slots, "form": "bf16_sound", "cap": args.ray_complete_cap,
                       "ms": c_ms,
                       "completed": int(ended.sum()), "hits": int(np.isfinite(t_c).sum()),
                       "rays_per_s": float(ended.sum()) / (c_ms / 1e3),

@@ -255,8 +255,14 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * center, point and noise operands split into BF16 hi/lo pairs and FP32
  * accumulation (about 16 significant bits per product), and |W| x_inf from
  * |W| and x_inf rounded up to BF16 (an upper bound of that term); plain
- * arithmetic otherwise, no rounding radius. BF16
- * needs affine-fixed arithmetic and a network whose hidden layers all have
+ * arithmetic otherwise, no rounding radius. SRA_PREC_BF16_SOUND is the same
+ * computation with every segment bound guaranteed: the rounding of the
+ * segment box and of the encoding, the products' and FP32 sums' errors
+ * (a-priori, from |W| (|c| + |A|) on the tensor cores) and the operands'
+ * BF16 storage go to x_inf, the activation rules are the outward-rounded
+ * ones (Chebyshev slope only), and the segment's range is rounded outward;
+ * the point test f(t + delta) stays a plain evaluation. Both BF16 forms
+ * need affine-fixed arithmetic and a network whose hidden layers all have
  * one width H in {128, 256, 512}, with 1 to 8 H -> H layers and an input
  * width (after the encoding) of at most 64; otherwise SRA_EUNSUPPORTED. A
  * bounded wait of that kernel that runs out is reported by sra_sync_status as

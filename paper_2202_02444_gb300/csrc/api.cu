@@ -482,6 +482,25 @@ void prepare_tc_rays(sra_net *n, const float *params) {
     t.din = n->din;
     t.pe = n->pe;
     t.status = (int *)((char *)n->tcr_buf + 3 * per_0 + 3 * nh * per_h);
+    // sound form: per linear layer of K inputs, D takes 2 K/16 MMA steps
+    // (W_b and W_r) and each |W| x sum of Dx K/16; each 16-deep step adds at
+    // most 17 * 2^-23 of its terms' sizes; W_b + W_r is within u_b^2 of W
+    {
+        const double u = std::ldexp(1.0, -24), ub = std::ldexp(1.0, -8);
+        auto layer = [&](int K, float &kx, float &rhok) {
+            const double gx = 17.0 * (K / 16.0) * std::ldexp(1.0, -23);
+            const double gacc = 17.0 * (2.0 * K / 16.0) * std::ldexp(1.0, -23);
+            const double k = 1.0 / (1.0 - gx) * (1.0 + 1e-6);
+            kx = (float)k;
+            rhok = (float)((ub * ub + gacc * (1.0 + 2.0 * ub)) * k * 1.001);
+        };
+        layer(64, t.kx0, t.rhok0);
+        layer(H, t.kx, t.rhok);
+        // output layer: 64-term fmaf parts, H/64 part adds, the pair sums of
+        // the operands and the final add
+        const double nsum = H + H / 64.0 + 3.0;
+        t.gam_out = (float)(nsum * u / (1.0 - nsum * u) * 1.001);
+    }
     cudaMemset(t.status, 0, sizeof(int));
     n->tcr_H = H;
     n->tcr_ok = true;
@@ -1214,13 +1233,16 @@ static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const floa
         o->max_iters < 1)
         return fail(SRA_EINVAL, "ray options out of range (delta, t_max, sigma0 > 0; eta+ >= 1; "
                                 "0 < eta- < 1; 0 < safety <= 1; max_iters >= 1)");
-    const bool tc = o->precision == SRA_PREC_BF16, fp64 = o->precision == SRA_PREC_FP64;
+    const bool sound = o->precision == SRA_PREC_BF16_SOUND;
+    const bool tc = o->precision == SRA_PREC_BF16 || sound, fp64 = o->precision == SRA_PREC_FP64;
     if (o->precision != SRA_PREC_FP32 && !tc && !fp64)
-        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32, FP64 or (tensor cores) BF16");
+        return fail(SRA_EUNSUPPORTED, "cast_rays runs in FP32, FP64 or (tensor cores) BF16 / BF16-sound");
     if (tc && (!n->tcr_ok || o->arith != SRA_ARITH_AFFINE_FIXED))
         return fail(SRA_EUNSUPPORTED, "BF16 cast_rays needs affine-fixed arithmetic and a net of "
                                       "uniform hidden width 128/256/512 with 1..%d hidden layers and "
                                       "input width <= %d", kMaxRayTc, tc_ray_max_din());
+    if (sound && o->slope != SRA_SLOPE_CHEBYSHEV)
+        return fail(SRA_EUNSUPPORTED, "BF16-sound cast_rays uses the Chebyshev slope");
     if (count > INT32_MAX) return fail(SRA_EINVAL, "n > 2^31 - 1");
     const bool recheck = o->recheck && !fp64;
     cudaStream_t st = as_stream(stream);
@@ -1272,7 +1294,7 @@ static sra_status cast_rays_impl(const sra_net *n, const sra_opts *o, const floa
         long long grid = num_sms();
         const long long need = (count + tc_ray_slots() - 1) / tc_ray_slots();
         if (grid > need) grid = need;
-        cudaError_t e = launch_tc_rays(n->tcr_H, p, (int)grid, st);
+        cudaError_t e = launch_tc_rays(n->tcr_H, sound, p, (int)grid, st);
         if (e != cudaSuccess) return fail(SRA_ECUDA, "tensor-core ray kernel launch: %s", cudaGetErrorString(e));
     } else {
         RayParams rp;

@@ -32,6 +32,7 @@
 // drains the copies and MMAs it started (bounded again), frees TMEM and exits.
 #include <cuda_bf16.h>
 
+#include "sound_rules.cuh"
 #include "sra_common.cuh"
 #include "tc_ptx.cuh"
 #include "tc_rays.h"
@@ -41,13 +42,16 @@ namespace tcr {
 
 constexpr int NR = 16;      // ray slots per CTA
 constexpr int NCOL = 96;    // operand rows of D: 6 per ray
-constexpr int NXI = 16;     // operand rows of Dx: 1 per ray
+// operand rows of Dx: x_inf of each ray (rounded up), and in the sound form
+// also |c| + |A| (rounded up), whose product with |W| bounds the layer's
+// rounding errors
+template <bool SOUND> constexpr int nxi() { return SOUND ? 32 : 16; }
 constexpr int MAXDIN = 64;  // input width (3 + 6 * octaves) bound: layer 0 has one K slice
 constexpr int TILE = 128 * 128;
 constexpr int kSmemCap = 232448;
 constexpr uint32_t kSpin = 1u << 22;
 enum { C_HI = 0, C_LO = 16, P_HI = 32, P_LO = 48, A_HI = 64, A_LO = 80 };
-enum { X_RU = 0 };
+enum { X_RU = 0, X_MAG = 16 };
 
 struct RaySlot {
     long long idx;
@@ -57,15 +61,17 @@ struct RaySlot {
 
 constexpr int align1k(int x) { return (x + 1023) & ~1023; }
 
-template <int H> struct RL {
+template <int H, bool SOUND> struct RL {
     static constexpr int MT = H / 128, S = H / 64;
+    static constexpr int NXI = nxi<SOUND>();
+    static constexpr int NK = SOUND ? 5 : 4;  // output-layer sums per ray
     static constexpr int XB_SLICE = NCOL * 128, XI_SLICE = NXI * 128;
     static constexpr int XB_OFF = 0;
     static constexpr int XI_OFF = XB_OFF + S * XB_SLICE;
     static constexpr int INP_OFF = XI_OFF + S * XI_SLICE;       // segment inputs [NR][12]
     static constexpr int NPART = H / 64;
-    static constexpr int OUTP_OFF = INP_OFF + NR * 12 * 4;       // output partial sums [4 NR][NPART]
-    static constexpr int WOUT_OFF = OUTP_OFF + 4 * NR * NPART * 4;
+    static constexpr int OUTP_OFF = INP_OFF + NR * 12 * 4;       // output partial sums [NK NR][NPART]
+    static constexpr int WOUT_OFF = OUTP_OFF + NK * NR * NPART * 4;
     static constexpr int RAY_OFF = WOUT_OFF + H * 4;
     static constexpr int BAR_OFF = RAY_OFF + NR * (int)sizeof(RaySlot);
     static constexpr int MISC_OFF = BAR_OFF + 256;
@@ -73,7 +79,8 @@ template <int H> struct RL {
     static constexpr int NSTG_FIT = (kSmemCap - 1024 - RING_OFF) / TILE;
     static constexpr int NSTG = NSTG_FIT >= 8 ? 8 : 4;  // 4 measured faster than 5 at H = 512
     static constexpr int ALLOC = RING_OFF + NSTG * TILE + 1024;
-    static constexpr int TCOLS = MT * 128;                       // TMEM: D (96) + Dx (16) per M-tile
+    static constexpr int TCOLS = MT * 128;                       // TMEM: D (96) + Dx (NXI) per M-tile
+    static_assert(NCOL + NXI <= 128, "TMEM columns");
     static_assert(NSTG_FIT >= 4, "weight ring");
     static_assert(MT == 1 || MT == 2 || MT == 4, "M tiles");
     static_assert(2 * NSTG + 2 <= 32, "barrier slots");
@@ -93,13 +100,25 @@ __device__ __forceinline__ float get_pair(const unsigned char *slice, int row_hi
            __bfloat162float(*(const __nv_bfloat16 *)(slice + ptx::sw128_offset((uint32_t)row_lo, kk)));
 }
 
-// Operand rows at K index k (the next layer's input k) for ray slot r.
-template <int H>
+// Operand rows at K index k (the next layer's input k) for ray slot r. The
+// sound form first adds to x_inf the residuals of the centre's and the noise
+// entry's BF16 hi/lo pairs (exact in FP32: the stored pair is c_hi + c_lo =
+// c - rc), then stores x_inf and |c| + |A| rounded up.
+template <int H, bool SOUND>
 __device__ __forceinline__ void write_rows(unsigned char *sm, int k, int r, float c, float A, float xi, float p) {
-    using L = RL<H>;
+    using L = RL<H, SOUND>;
     const uint32_t kk = (uint32_t)(k & 63);
     unsigned char *xb = sm + L::XB_OFF + (k >> 6) * L::XB_SLICE;
     unsigned char *xs = sm + L::XI_OFF + (k >> 6) * L::XI_SLICE;
+    if (SOUND) {
+        const float ch = __bfloat162float(__float2bfloat16_rn(c)), ah = __bfloat162float(__float2bfloat16_rn(A));
+        const float cr = c - ch, ar = A - ah;  // exact
+        const float rc = cr - __bfloat162float(__float2bfloat16_rn(cr)), ra = ar - __bfloat162float(__float2bfloat16_rn(ar));
+        const float res = ru_add(fabsf(rc), fabsf(ra));
+        xi = ru_add(xi, res);
+        const float mag = ru_add(ru_add(fabsf(c), fabsf(A)), res);  // >= |stored c| + |stored A|
+        *(__nv_bfloat16 *)(xs + ptx::sw128_offset((uint32_t)(X_MAG + r), kk)) = __float2bfloat16_ru(mag);
+    }
     put_pair(xb, C_HI + r, C_LO + r, kk, c);
     put_pair(xb, P_HI + r, P_LO + r, kk, p);
     put_pair(xb, A_HI + r, A_LO + r, kk, A);
@@ -120,6 +139,25 @@ __device__ __forceinline__ void activate(int act, int slope, float &c, float &A,
     p = act_eval<float>(act, p);
 }
 
+// The sound form of `activate` (Chebyshev slope): the rules of
+// sound_rules.cuh on the outward-rounded range c +- (|A| + xi); the new
+// symbol joins x_inf (affine-fixed), and the FP32 product al * A adds 2^-24
+// of its size (its BF16 hi/lo storage is added by write_rows). The point
+// value takes the plain activation.
+__device__ __forceinline__ void activate_sound(int act, float &c, float &A, float &xi, float &p) {
+    if (act == SRA_ACT_IDENTITY) return;
+    const float sa = fabsf(A);
+    constexpr float kProd = 5.9604645e-08f * 1.001f;
+    float al, ga, c2, xo;
+    if (act == SRA_ACT_ELU) elu_rule<true>(sa, c, xi, kProd, al, ga, c2, xo);
+    else if (act == SRA_ACT_SIN) sin_rule<true>(sa, c, xi, kProd, al, ga, c2, xo);
+    else relu_rule<true>(sa, c, xi, kProd, al, ga, c2, xo);
+    A = al * A;
+    c = c2;
+    xi = ru_add(xo, ga);
+    p = act_eval<float>(act, p);
+}
+
 // A ring unit: one 128 x 64 tile (M tile m, K slice s) of one of the three
 // matrices of linear layer `layer` (0 W_b, 1 W_r: into D; 2 |W|_ru: into
 // Dx). Within a layer the units run K slice by K slice, M tile by M tile, in
@@ -131,8 +169,8 @@ struct Unit {
     int layer, s, m, which;
 };
 
-template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
-    using L = RL<H>;
+template <int H, bool SOUND> __device__ __forceinline__ Unit unit_of(int layer, int u) {
+    using L = RL<H, SOUND>;
     Unit r;
     r.layer = layer;
     const int ms = u / 3, w = u - 3 * ms;
@@ -142,8 +180,8 @@ template <int H> __device__ __forceinline__ Unit unit_of(int layer, int u) {
     return r;
 }
 
-template <int H> __device__ __forceinline__ int units_of(int layer) {
-    using L = RL<H>;
+template <int H, bool SOUND> __device__ __forceinline__ int units_of(int layer) {
+    using L = RL<H, SOUND>;
     return layer == 0 ? 3 * L::MT : 3 * L::MT * L::S;
 }
 
@@ -154,8 +192,8 @@ struct RingPos {
     uint32_t ph;
 };
 
-template <int H> __device__ __forceinline__ void advance(RingPos &r) {
-    if (++r.st == RL<H>::NSTG) {
+template <int H, bool SOUND> __device__ __forceinline__ void advance(RingPos &r) {
+    if (++r.st == RL<H, SOUND>::NSTG) {
         r.st = 0;
         r.ph ^= 1u;
     }
@@ -171,30 +209,30 @@ struct Cursor {
 
 // Issue the copy of the cursor's unit into its stage once the MMAs of that
 // stage's previous use have completed; advance the cursor.
-template <int H>
+template <int H, bool SOUND>
 __device__ __forceinline__ bool ring_load(unsigned char *sm, uint64_t *bars, const TcRayParams &p, int NL,
                                           Cursor &c) {
-    using L = RL<H>;
+    using L = RL<H, SOUND>;
     const int st = c.pos.st;
     if (!ptx::mbar_wait(&bars[L::NSTG + st], c.pos.ph ^ 1u, kSpin)) return false;
-    const Unit u = unit_of<H>(c.layer, c.u);
+    const Unit u = unit_of<H, SOUND>(c.layer, c.u);
     const TcLayerMaps &mp = u.layer == 0 ? p.first : p.hidden[u.layer - 1];
     const CUtensorMap *map = u.which == 0 ? &mp.wb : (u.which == 1 ? &mp.wr : &mp.wa);
     unsigned char *dst = sm + L::RING_OFF + st * TILE;
     ptx::mbar_arrive_expect_tx(&bars[st], TILE);
     ptx::tma_load_2d(dst, map, u.s * 64, u.m * 128, &bars[st]);
     ++c.issued;
-    advance<H>(c.pos);
-    if (++c.u == units_of<H>(c.layer)) {
+    advance<H, SOUND>(c.pos);
+    if (++c.u == units_of<H, SOUND>(c.layer)) {
         c.u = 0;
         c.layer = (c.layer == NL) ? 0 : c.layer + 1;
     }
     return true;
 }
 
-template <int H>
+template <int H, bool SOUND>
 __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ TcRayParams p) {
-    using L = RL<H>;
+    using L = RL<H, SOUND>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, i = tid;
@@ -266,9 +304,18 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                     in[d] = o + (s.t + s.sigma / 2.f) * r;
                     in[3 + d] = (s.sigma / 2.f) * r;
                     in[6 + d] = o + (s.t + p.delta) * r;
+                    if (SOUND) {
+                        // the segment's points o + u r, u in [t, t + sigma], lie within
+                        // in[9+d] of the box in[d] +- |in[3+d]|: the three roundings of
+                        // the centre (the sum t + sigma/2, the product, the add of o)
+                        // and the product of the half-width
+                        const float m = fabsf((s.t + s.sigma / 2.f) * r);
+                        in[9 + d] = ru_fma(ru_add(fabsf(in[d]), 2.f * m), 5.9604645e-08f * 1.001f,
+                                           __fmul_ru(fabsf(in[3 + d]), 5.9604645e-08f * 1.001f));
+                    }
                 }
             } else {
-                for (int d = 0; d < 9; ++d) in[d] = 0.f;
+                for (int d = 0; d < 12; ++d) in[d] = 0.f;
             }
         }
         const bool any = __syncthreads_or(tid < NR && slots[tid].live);
@@ -282,25 +329,37 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 if (j < 3) {
                     c = in[j];
                     A = in[3 + j];
+                    if (SOUND) xi = in[9 + j];
                     pt = in[6 + j];
                 } else {
                     const int q = j - 3, k = q / 6, d = q % 3;
                     const float sc = (float)(1 << k), sh = ((q % 6) >= 3) ? 0.5f : 0.f;
                     const float ct = sc * in[d] + sh, at = sc * in[3 + d];
-                    const float rad = fabsf(at);
-                    float a, b, gm;
-                    linearize_sinpi<float>(ct - rad, ct + rad, a, b, gm);
-                    c = a * ct + b;
-                    A = at * a;
-                    xi = fabsf(gm);
+                    if (SOUND) {
+                        // sc * in[d] and sc * in[3+d] are exact (sc = 2^k); the add of
+                        // sh rounds once
+                        const float xin = ru_fma(fabsf(ct), 5.9604645e-08f * 1.001f, sc * in[9 + d]);
+                        float al, ga, c2, xo;
+                        sinpi_rule_sound(fabsf(at), ct, xin, 5.9604645e-08f * 1.001f, al, ga, c2, xo);
+                        c = c2;
+                        A = at * al;
+                        xi = ru_add(xo, ga);
+                    } else {
+                        const float rad = fabsf(at);
+                        float a, b, gm;
+                        linearize_sinpi<float>(ct - rad, ct + rad, a, b, gm);
+                        c = a * ct + b;
+                        A = at * a;
+                        xi = fabsf(gm);
+                    }
                     pt = sinpi_t(sc * in[6 + d] + sh);
                 }
             }
-            write_rows<H>(sm, j, r, c, A, xi, pt);  // zero rows past din
+            write_rows<H, SOUND>(sm, j, r, c, A, xi, pt);  // zero rows past din
         }
         // ---- every layer but the output one on the tensor cores --------------
         for (int l = 0; l <= NL; ++l) {
-            const uint32_t U = (uint32_t)units_of<H>(l);
+            const uint32_t U = (uint32_t)units_of<H, SOUND>(l);
             ptx::fence_proxy_async();  // operand writes -> async proxy
             ptx::tc_fence_before();    // TMEM reads of the previous layer are done
             __syncthreads();
@@ -309,11 +368,11 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 bool ok = true;
                 // copies run up to NSTG - 1 units past this layer's end
                 while (ok && (int32_t)(cur.issued - (gbase + U + (L::NSTG - 1))) < 0)
-                    ok = ring_load<H>(sm, bars, p, NL, cur);
+                    ok = ring_load<H, SOUND>(sm, bars, p, NL, cur);
                 if (!ok) fail(6);
             } else if (issuer) {
                 bool ok = true;
-                const uint32_t iD = ptx::idesc_bf16(128, NCOL), iX = ptx::idesc_bf16(128, NXI);
+                const uint32_t iD = ptx::idesc_bf16(128, NCOL), iX = ptx::idesc_bf16(128, L::NXI);
                 // two consecutive units at a time (they feed different
                 // accumulators): their MMAs alternate; an odd last unit alone
                 for (uint32_t k = 0; k < U && ok;) {
@@ -324,9 +383,9 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                     bool first[2];
                     for (int j = 0; j < nj; ++j) {
                         pos[j] = ipos;
-                        advance<H>(ipos);
+                        advance<H, SOUND>(ipos);
                         if (!ptx::mbar_wait(&bars[pos[j].st], pos[j].ph, kSpin)) { ok = false; break; }
-                        const Unit u = unit_of<H>(l, (int)k + j);
+                        const Unit u = unit_of<H, SOUND>(l, (int)k + j);
                         const bool dx = u.which == 2;
                         const uint32_t b_addr = dx ? ptx::smem_u32(sm + L::XI_OFF + u.s * L::XI_SLICE)
                                                    : ptx::smem_u32(sm + L::XB_OFF + u.s * L::XB_SLICE);
@@ -361,6 +420,9 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
             // epilogue: neuron i of every ray slot (the layer's operands are free)
             const float bias = __ldg(p.b[l] + i);
             const int act = p.act[l];
+            // sound form: the FP32 accumulation factor of the Dx sums and the
+            // rounding errors of D per unit of |W| (|c| + |A|), by layer depth
+            const float kx = l == 0 ? p.kx0 : p.kx, rk = l == 0 ? p.rhok0 : p.rhok;
 #pragma unroll 1
             for (int g = 0; g < NR / 8; ++g) {
                 float v[64];
@@ -372,6 +434,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 ptx::tmem_ld8(tl + A_HI + r0, v + 32);
                 ptx::tmem_ld8(tl + A_LO + r0, v + 40);
                 ptx::tmem_ld8(tl + NCOL + X_RU + r0, v + 48);
+                if (SOUND) ptx::tmem_ld8(tl + NCOL + X_MAG + r0, v + 56);
                 ptx::tmem_wait_ld();
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
@@ -379,17 +442,28 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                     float pp = (v[16 + r] + v[24 + r]) + bias;
                     float A = v[32 + r] + v[40 + r];
                     float xi = v[48 + r];
-                    activate(act, p.slope, c, A, xi, pp);
-                    write_rows<H>(sm, i, r0 + r, c, A, xi, pp);
+                    if (SOUND) {
+                        // |W| x_inf and the layer's rounding errors from the Dx
+                        // sums, each scaled for its FP32 accumulation; the two adds
+                        // of the centre and the one of the noise pair
+                        xi = ru_fma(v[56 + r], rk, ru_mul(xi, kx));
+                        xi = ru_fma(ru_add(2.f * fabsf(c), fabsf(bias)), 5.9604645e-08f * 1.001f, xi);
+                        xi = ru_fma(fabsf(A), 5.9604645e-08f * 1.001f, xi);
+                        activate_sound(act, c, A, xi, pp);
+                    } else {
+                        activate(act, p.slope, c, A, xi, pp);
+                    }
+                    write_rows<H, SOUND>(sm, i, r0 + r, c, A, xi, pp);
                 }
             }
         }
         __syncthreads();
         if (*abort_flag) break;
-        // ---- output layer (H -> 1): 4 sums per ray, H/64 parts of 64 inputs each
+        // ---- output layer (H -> 1): 4 sums per ray (5 in the sound form: also
+        // sum |w| (|c| + |A|)), H/64 parts of 64 inputs each
         {
             const int q = tid & 63, part = tid >> 6, r = q >> 2, kind = q & 3;
-            float acc = 0.f;
+            float acc = 0.f, accm = 0.f;
             for (int j = part * 64; j < part * 64 + 64; ++j) {
                 const uint32_t kk = (uint32_t)(j & 63);
                 const unsigned char *xb = sm + L::XB_OFF + (j >> 6) * L::XB_SLICE;
@@ -397,25 +471,41 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 const float w = wout[j];
                 if (kind == 0) acc = fmaf(w, get_pair(xb, C_HI + r, C_LO + r, kk), acc);
                 else if (kind == 1) acc = fmaf(w, get_pair(xb, A_HI + r, A_LO + r, kk), acc);
-                else if (kind == 2)
+                else if (kind == 2) {
                     acc = fmaf(fabsf(w),
                                __bfloat162float(*(const __nv_bfloat16 *)(xs + ptx::sw128_offset((uint32_t)(X_RU + r), kk))),
                                acc);
-                else acc = fmaf(w, get_pair(xb, P_HI + r, P_LO + r, kk), acc);
+                    if (SOUND)
+                        accm = fmaf(fabsf(w),
+                                    __bfloat162float(
+                                        *(const __nv_bfloat16 *)(xs + ptx::sw128_offset((uint32_t)(X_MAG + r), kk))),
+                                    accm);
+                } else acc = fmaf(w, get_pair(xb, P_HI + r, P_LO + r, kk), acc);
             }
-            outp[q * L::NPART + part] = acc;
+            outp[(r * L::NK + kind) * L::NPART + part] = acc;
+            if (SOUND && kind == 2) outp[(r * L::NK + 4) * L::NPART + part] = accm;
         }
         __syncthreads();
         // ---- march step of each live slot (Proc. 2) -------------------------------
         if (tid < NR && slots[tid].live) {
             RaySlot &s = slots[tid];
-            float sums[4];
-            for (int kind = 0; kind < 4; ++kind) {
+            float sums[5];
+            for (int kind = 0; kind < L::NK; ++kind) {
                 float a = 0.f;
-                for (int part = 0; part < L::NPART; ++part) a += outp[(tid * 4 + kind) * L::NPART + part];
+                for (int part = 0; part < L::NPART; ++part) a += outp[(tid * L::NK + kind) * L::NPART + part];
                 sums[kind] = a;
             }
-            const float y0 = sums[0] + p.bout, rad = fabsf(sums[1]) + sums[2], fc = sums[3] + p.bout;
+            const float y0 = sums[0] + p.bout, fc = sums[3] + p.bout;
+            float rad = fabsf(sums[1]) + sums[2];
+            if (SOUND) {
+                // the output sums' FP32 errors: within gam_out of sum |w| (|c| + |A|)
+                // (the fifth sum, itself scaled up) and |bout|; the x_inf sum
+                // scaled up; the add of the bias
+                const float g1 = 1.f + p.gam_out;
+                rad = ru_add(fabsf(sums[1]), ru_mul(sums[2], g1));
+                rad = ru_fma(ru_fma(sums[4], g1, fabsf(p.bout)), p.gam_out, rad);
+                rad = ru_fma(fabsf(y0), 5.9604645e-08f * 1.001f, rad);
+            }
             s.iters += 1;
             if (p.flag_list && near_zero_step<float>(y0, rad, p.band)) s.flag = 1;
             bool done = false;
@@ -424,7 +514,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 done = true;
                 result = s.t;
             } else {
-                const int k = classify_range(y0 - rad, y0 + rad);
+                const int k = SOUND ? classify_range(rd_add(y0, -rad), ru_add(y0, rad)) : classify_range(y0 - rad, y0 + rad);
                 float sstar;
                 if (k != SRA_UNKNOWN) { sstar = s.sigma; s.sigma *= p.eta_plus; }
                 else { sstar = 0.f; s.sigma *= p.eta_minus; }
@@ -458,7 +548,7 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
                 atomicExch(p.status, 10);
                 break;
             }
-            advance<H>(r);
+            advance<H, SOUND>(r);
         }
     }
     __syncwarp();
@@ -470,26 +560,31 @@ __global__ void __launch_bounds__(H, 1) tc_ray_kernel(const __grid_constant__ Tc
 
 }  // namespace tcr
 
-int tc_ray_smem_bytes(int H) {
-    return H == 512 ? tcr::RL<512>::ALLOC : (H == 256 ? tcr::RL<256>::ALLOC : (H == 128 ? tcr::RL<128>::ALLOC : 0));
+int tc_ray_smem_bytes(int H, bool sound) {
+    if (sound)
+        return H == 512 ? tcr::RL<512, true>::ALLOC
+                        : (H == 256 ? tcr::RL<256, true>::ALLOC : (H == 128 ? tcr::RL<128, true>::ALLOC : 0));
+    return H == 512 ? tcr::RL<512, false>::ALLOC
+                    : (H == 256 ? tcr::RL<256, false>::ALLOC : (H == 128 ? tcr::RL<128, false>::ALLOC : 0));
 }
 
 int tc_ray_max_din() { return tcr::MAXDIN; }
 
 int tc_ray_slots() { return tcr::NR; }
 
-template <int H> static cudaError_t launch_r(const TcRayParams &p, int grid, cudaStream_t st) {
-    const int smem = tc_ray_smem_bytes(H);
-    cudaError_t e = cudaFuncSetAttribute(tcr::tc_ray_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <int H, bool SOUND> static cudaError_t launch_r(const TcRayParams &p, int grid, cudaStream_t st) {
+    const int smem = tcr::RL<H, SOUND>::ALLOC;
+    cudaError_t e =
+        cudaFuncSetAttribute(tcr::tc_ray_kernel<H, SOUND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    tcr::tc_ray_kernel<H><<<grid, H, smem, st>>>(p);
+    tcr::tc_ray_kernel<H, SOUND><<<grid, H, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_rays(int H, const TcRayParams &p, int grid, cudaStream_t st) {
-    if (H == 512) return launch_r<512>(p, grid, st);
-    if (H == 256) return launch_r<256>(p, grid, st);
-    if (H == 128) return launch_r<128>(p, grid, st);
+cudaError_t launch_tc_rays(int H, bool sound, const TcRayParams &p, int grid, cudaStream_t st) {
+    if (H == 512) return sound ? launch_r<512, true>(p, grid, st) : launch_r<512, false>(p, grid, st);
+    if (H == 256) return sound ? launch_r<256, true>(p, grid, st) : launch_r<256, false>(p, grid, st);
+    if (H == 128) return sound ? launch_r<128, true>(p, grid, st) : launch_r<128, false>(p, grid, st);
     return cudaErrorInvalidValue;
 }
 

@@ -39,11 +39,16 @@ struct TcRayParams {
     // appended once, when it ends, to flag_list[atomicAdd(flag_count, 1)]
     int *flag_list, *flag_count;
     float band;
+    // sound form (BF16 with a rounding radius): FP32 accumulation factors of
+    // the |W| x_inf sums (layer 0, hidden layers), the products' rounding
+    // errors per unit of |W| (|c| + |A|) times that factor, and the output
+    // layer's FP32 dot-product error factor
+    float kx0, kx, rhok0, rhok, gam_out;
 };
 
-int tc_ray_smem_bytes(int H);
+int tc_ray_smem_bytes(int H, bool sound);
 int tc_ray_max_din();
 int tc_ray_slots();  // rays per CTA
-cudaError_t launch_tc_rays(int H, const TcRayParams &p, int grid, cudaStream_t st);
+cudaError_t launch_tc_rays(int H, bool sound, const TcRayParams &p, int grid, cudaStream_t st);
 
 }  // namespace sra

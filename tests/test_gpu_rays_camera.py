@@ -1,6 +1,7 @@
 """Finished camera rays of the 39(PE)-[512]x6-1 ELU network (the 1920x1080
-ray-casting workload) on the tensor-core CastRay kernel against the FP64
-oracle (Proc. 2, App. B step rule).
+ray-casting workload) on the tensor-core CastRay kernel, plain BF16 and
+BF16-sound (segment bounds with the a-priori rounding radius), against the
+FP64 oracle (Proc. 2, App. B step rule).
 
 tests/golden/camera_rays_elu512x6_pe.json holds the oracle's CastRay of 64
 pixels (an 8 x 8 grid of stride 64 around the image centre), delta 1e-4,
@@ -38,7 +39,8 @@ def sra():
     return s
 
 
-def test_camera_rays_to_the_end(sra):
+@pytest.mark.parametrize("precision", ["bf16", "bf16_sound"])
+def test_camera_rays_to_the_end(sra, precision):
     g = json.load(open(GOLDEN))
     t_ref = np.array([float(x) for x in g["t"]])
     status = np.array(g["status"])
@@ -53,7 +55,7 @@ def test_camera_rays_to_the_end(sra):
     net = sra.Net(wl.net_elu512x6_pe())
     try:
         t, it = sra.cast_rays(net, torch.from_numpy(o[idx]).cuda(), torch.from_numpy(d[idx]).cuda(),
-                              arith="fixed", precision="bf16", delta=g["delta"], t_max=g["t_max"],
+                              arith="fixed", precision=precision, delta=g["delta"], t_max=g["t_max"],
                               sigma0=g["sigma0"], eta_plus=g["eta_plus"], eta_minus=g["eta_minus"],
                               safety=g["safety"], max_iters=g["max_iters"])
         sra.sync_status(net)
@@ -69,7 +71,7 @@ def test_camera_rays_to_the_end(sra):
     with np.errstate(invalid="ignore"):
         far = hit_g & hit_r & (np.abs(t[0] - t_ref) > g["delta"] * 1.0001 + 1e-6)
     mism = (hit_g != hit_r) | np.isnan(t[0]) | far
-    print(f"{n} rays: hits {hit_g.sum()} (oracle {hit_r.sum()}), differing {mism.sum()}, "
+    print(f"{precision}: {n} rays: hits {hit_g.sum()} (oracle {hit_r.sum()}), differing {mism.sum()}, "
           f"|dt| max {np.max(np.abs(t[0][hit_g & hit_r] - t_ref[hit_g & hit_r])):.2e}, "
           f"iterations GPU median {np.median(it[0]):.0f} / oracle {np.median(g['iters']):.0f}")
     assert not np.any(mism & (margin >= BAND)), np.nonzero(mism & (margin >= BAND))[0]

@@ -1,6 +1,9 @@
 """GPU parity of the tensor-core CastRay path (precision "bf16": split-BF16
-hidden layers on tcgen05, FP32 elsewhere) against the FP64 oracle and
-against the FP32 SIMT ray kernel (Proc. 2)."""
+hidden layers on tcgen05, FP32 elsewhere; "bf16_sound": the same with an
+a-priori rounding radius on every segment bound) against the FP64 oracle,
+an analytic plane, and the FP32 SIMT ray kernel (Proc. 2)."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -30,19 +33,72 @@ def cast(sra, mlp, o, d, **kw):
     return t.cpu().numpy(), it.cpu().numpy()
 
 
+@pytest.mark.parametrize("precision", ["bf16", "bf16_sound"])
 @pytest.mark.parametrize("width,depth,act,pe", [
     (128, 3, "relu", 0),
     (128, 4, "elu", 3),
     (128, 3, "sin", 0),
     (256, 3, "relu", 2),
+    (512, 3, "elu", 2),
 ])
-def test_tc_rays_vs_oracle(sra, width, depth, act, pe):
+def test_tc_rays_vs_oracle(sra, width, depth, act, pe, precision):
+    """Hit / miss and t within delta against the oracle's CastRay. The sound
+    form's segment bounds carry the a-priori rounding radius, so they decide
+    fewer segments and the march takes more steps: it runs without an
+    effective cap (t_max / delta + 2000 iterations)."""
     mlp = wl.make_mlp([width] * depth, act, seed=31 + width + depth, pe_octaves=pe)
     o, d = wl.sphere_rays(203, seed=8, radius=2.0)  # ragged against 8 slots per CTA
-    t, it = cast(sra, mlp, o, d, arith="fixed", precision="bf16", delta=1e-3, max_iters=4000)
-    ref = oracle.cast_rays(mlp, o, d, "fixed", delta=1e-3, max_iters=4000)
+    cap = 4000 if precision == "bf16" else 12000
+    t, it = cast(sra, mlp, o, d, arith="fixed", precision=precision, delta=1e-3, max_iters=cap)
+    ref = oracle.cast_rays(mlp, o, d, "fixed", delta=1e-3, max_iters=cap)
     check(t, ref, 1e-3, 1e-3, max_frac=0.05)
     assert np.isfinite(t).sum() + np.isinf(t).sum() > 150
+
+
+def plane_net(width, nv, b, M=16.0):
+    """f(x) = nv . x + b through two ReLU layers of the given width: neuron 0
+    carries nv . x + b + M (positive on every ray's path, so both ReLUs act
+    as the identity there) and the output subtracts M; the other neurons are
+    zero."""
+    W0 = np.zeros((width, 3))
+    W0[0] = nv
+    b0 = np.zeros(width)
+    b0[0] = b + M
+    W1 = np.zeros((width, width))
+    W1[0, 0] = 1.0
+    W2 = np.zeros((1, width))
+    W2[0, 0] = 1.0
+    return wl.make_custom_mlp([3, width, width, 1], [wl.ACT_RELU, wl.ACT_RELU],
+                              [(W0, b0), (W1, np.zeros(width)), (W2, np.array([-M]))])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16_sound"])
+@pytest.mark.parametrize("width", [128, 512])
+def test_tc_rays_plane_analytic(sra, width, precision):
+    """A plane through the tensor-core path: segment bounds of a linear
+    function decide their sign (up to the rounding radius), so the march
+    takes long steps, and every hit lies within delta after the analytic
+    crossing t*, none before it (Sec. 4.1's delta semantics), up to the
+    precision of the point test: f at t + delta is evaluated with BF16 hi/lo
+    operands (16 significant bits, here about 1e-4 in t at |x| ~ 10). A
+    sound segment bound that wrongly decided a segment holding the crossing
+    would step over it by more than that."""
+    nv = np.array([0.3, -0.5, 0.8])
+    mlp = plane_net(width, nv, -0.1)
+    o, d = wl.sphere_rays(300, seed=3)
+    t, it = cast(sra, mlp, o, d, arith="fixed", precision=precision, delta=1e-3, max_iters=20000)
+    n32 = nv.astype(np.float32).astype(np.float64)
+    tstar = -(o.astype(np.float64) @ n32 + float(np.float32(-0.1))) / (d.astype(np.float64) @ n32)
+    hits = 0
+    for i in range(len(o)):
+        if 1e-3 < tstar[i] < 10 - 1e-2:
+            assert t[i] < tstar[i] + 2e-4 and tstar[i] <= t[i] + 1e-3 + 2e-4, (i, t[i], tstar[i])
+            hits += 1
+        elif tstar[i] < 0 or tstar[i] > 10.1:
+            assert math.isinf(t[i]), (i, t[i], tstar[i])
+    assert hits > 50
+    # long steps: far fewer iterations than t / delta
+    assert np.median(it) < 100, np.median(it)
 
 
 def test_tc_rays_relu256x8(sra):
@@ -92,14 +148,15 @@ def test_tc_rays_iteration_cap(sra):
 def test_tc_rays_unsupported(sra):
     o, d = wl.sphere_rays(8, seed=5, radius=2.0)
     ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
-    cases = [(wl.make_mlp([128, 64, 128], "relu", seed=1), "fixed"),  # non-uniform width
-             (wl.make_mlp([96] * 3, "relu", seed=1), "fixed"),        # width not 128/256/512
-             (wl.make_mlp([128] * 3, "relu", seed=1), "truncate")]    # not affine-fixed
-    for mlp, arith in cases:
+    cases = [(wl.make_mlp([128, 64, 128], "relu", seed=1), "fixed", "bf16", "chebyshev"),  # non-uniform width
+             (wl.make_mlp([96] * 3, "relu", seed=1), "fixed", "bf16", "chebyshev"),       # width not 128/256/512
+             (wl.make_mlp([128] * 3, "relu", seed=1), "truncate", "bf16", "chebyshev"),   # not affine-fixed
+             (wl.make_mlp([128] * 3, "relu", seed=1), "fixed", "bf16_sound", "minrange")]  # sound: Chebyshev only
+    for mlp, arith, prec, slope in cases:
         net = sra.Net(mlp)
         try:
             with pytest.raises(sra.SraError) as e:
-                sra.cast_rays(net, ot, dt, arith=arith, K=4, precision="bf16")
+                sra.cast_rays(net, ot, dt, arith=arith, K=4, precision=prec, slope=slope)
             assert e.value.code == sra.EUNSUPPORTED
         finally:
             net.close()
