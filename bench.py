@@ -68,11 +68,12 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true,ReLU>": {"sha1": "a52d8faed401fdfe9dcb10f4a600111171d4a161", "bytes": 2968832,
+    "tc_bound_kernel<256,true,ReLU>": {"sha1": "7416bf556b4edfe805fbc55df0e60cb176f7a40e", "bytes": 3286016,
                                        "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_bound_impl.cuh",
-                    "paper_2202_02444_gb300/csrc/tc_ptx.cuh", "paper_2202_02444_gb300/csrc/tc_bound.h")
+                    "paper_2202_02444_gb300/csrc/sound_rules.cuh", "paper_2202_02444_gb300/csrc/tc_ptx.cuh",
+                    "paper_2202_02444_gb300/csrc/tc_bound.h")
 
 
 def sources_sha1(paths):
