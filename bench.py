@@ -213,14 +213,15 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
     """Poisson request traces (seed 5) against 16 resident networks through
     sra_serve: a third each of 64x64 ray tiles (cap 200 iterations per ray),
     batches of U[256, 65536] boxes and leaf-extraction jobs to depth 9 (frontier
-    capacity 2^20 nodes per level). Each request takes the BF16 form (tensor
-    cores) with probability 1/2 where its network has that kernel, else FP32.
+    capacity 2^20 nodes per level). Each ray or box request takes the
+    BF16-sound form (tensor cores) with probability 1/2 where its network has
+    that kernel, else FP32.
     Returns p50 / p99 latency (arrival to completion) and throughput per rate."""
     mlps = serving_nets()
     nets = [sra.Net(m) for m in mlps]
     forms = [sra.make_opts(arith="fixed", delta=1e-3, max_iters=200),                     # rays FP32
              sra.make_opts(arith="truncate", K=16),                                       # boxes / leaves FP32
-             sra.make_opts(arith="fixed", delta=1e-3, max_iters=200, precision="bf16"),   # rays BF16
+             sra.make_opts(arith="fixed", delta=1e-3, max_iters=200, precision="bf16_sound"),  # rays BF16-sound
              sra.make_opts(arith="truncate", K=64, precision="bf16_sound", recheck=True)]  # boxes BF16-sound
 
     def uniform(m, H):
@@ -234,8 +235,8 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
                        "39(PE)-[512]x6-1, seeds 2..5); Poisson arrivals (seed 5); 1/3 each: 64x64 "
                        "camera ray tile (affine-fixed, delta 1e-3, cap 200 iterations), U[256,65536] "
                        "boxes (affine-truncate K=16 FP32 / K=64 BF16-sound), leaf extraction to depth 9 "
-                       "(K=16, frontier cap 2^20 per level); BF16 form for half the requests whose net "
-                       "has that kernel",
+                       "(K=16, frontier cap 2^20 per level); BF16-sound form (rays and boxes) for half "
+                       "the requests whose net has that kernel",
            "slots": slots, "frontier_budget_bytes": budget, "rates": []}
     for lam in rates:
         rng = np.random.default_rng(5)

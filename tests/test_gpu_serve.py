@@ -31,7 +31,8 @@ def nets(sra):
 def forms(sra):
     return [sra.make_opts(arith="fixed", delta=1e-3, max_iters=300),              # 0: FP32 fixed
             sra.make_opts(arith="truncate", K=16),                                # 1: FP32 truncate
-            sra.make_opts(arith="fixed", precision="bf16", delta=1e-3, max_iters=300)]  # 2: BF16 rays
+            sra.make_opts(arith="fixed", precision="bf16", delta=1e-3, max_iters=300),  # 2: BF16 rays
+            sra.make_opts(arith="fixed", precision="bf16_sound", delta=1e-3, max_iters=300)]  # 3: BF16-sound rays
 
 
 def make_trace(sra, n_req, seed, spacing=0.0):
@@ -49,7 +50,8 @@ def make_trace(sra, n_req, seed, spacing=0.0):
             o, d = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
             t = torch.full((n,), -7.0, device="cuda")
             it = torch.full((n,), -7, dtype=torch.int32, device="cuda")
-            form = 2 if net in (1, 2) and rng.random() < 0.5 else 0
+            u = rng.random()
+            form = (2 if u < 0.25 else 3) if net in (1, 2) and u < 0.5 else 0
             reqs.append(sra.ray_request(net, form, arrival, o, d, t, it))
             bufs.append(("rays", net, form, (o, d), (t, it)))
         elif kind == sra.REQ_BOXES:
