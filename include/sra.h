@@ -479,6 +479,14 @@ sra_status sra_test_fail_allocs(int32_t n);
  * Errors: SRA_EINVAL for spins outside [0, 2^20]. */
 sra_status sra_test_tc_stall(int32_t spins);
 
+/* Diagnostics (the paper has no counterpart): y[i] = f(x[i]) on the device
+ * for the FP32 math functions whose errors the sound activation rules pad:
+ * fn 0 sinf, 1 cosf, 2 sinpif, 3 acosf, 4 expm1f, 5 expf, 6 logf. x, y:
+ * device float[n]. Asynchronous on `stream`. Errors: SRA_EINVAL (unknown fn,
+ * n < 0, null pointers with n > 0), SRA_ECUDA. */
+#define SRA_MATH_N 7
+sra_status sra_test_math_f32(int32_t fn, const float *x, int64_t n, float *y, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

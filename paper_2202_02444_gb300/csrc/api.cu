@@ -1718,6 +1718,17 @@ extern "C" sra_status sra_test_tc_stall(int32_t spins) {
     return SRA_OK;
 }
 
+extern "C" sra_status sra_test_math_f32(int32_t fn, const float *x, int64_t n, float *y, void *stream) {
+    g_err.clear();
+    if (fn < 0 || fn >= SRA_MATH_N) return fail(SRA_EINVAL, "math function %d outside [0, %d)", fn, SRA_MATH_N);
+    if (n < 0) return fail(SRA_EINVAL, "n < 0");
+    if (n == 0) return SRA_OK;
+    if (!x || !y) return fail(SRA_EINVAL, "null x/y");
+    cudaError_t e = launch_math_f32(fn, x, n, y, as_stream(stream));
+    if (e != cudaSuccess) return fail(SRA_ECUDA, "math kernel launch: %s", cudaGetErrorString(e));
+    return SRA_OK;
+}
+
 extern "C" sra_status sra_test_fail_allocs(int32_t n) {
     g_err.clear();
     if (n < 0) return fail(SRA_EINVAL, "n < 0");

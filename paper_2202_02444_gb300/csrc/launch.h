@@ -15,6 +15,9 @@ __host__ __device__ constexpr int engine_row_stride(int kmax) { return ((kmax + 
 // KMAX values the engine is instantiated for.
 constexpr int kKmaxList[] = {1, 4, 8, 16, 32, 64, 128};
 
+// y = f(x) for the FP32 math functions of sra_test_math_f32 (math_probe.cu).
+cudaError_t launch_math_f32(int fn, const float *x, long long n, float *y, cudaStream_t st);
+
 cudaError_t launch_bound_f32(int kmax, const NetDev &net, const BoxSrc &src, const BoundOut &out,
                              const RangeCfg &cfg, long long grid, cudaStream_t st);
 cudaError_t launch_bound_f64(int kmax, const NetDev &net, const BoxSrc &src, const BoundOut &out,
