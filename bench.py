@@ -566,6 +566,22 @@ def cpu_baseline(mlp, fr_nodes, K, nsample, nsample_1core):
     return line
 
 
+def cpu_baseline_rays(mlp, o, d, nrays=32, iters=200):
+    """The FP64 oracle's CastRay (Proc. 2) on a bounded sample of the camera
+    tile's rays (each capped at `iters` iterations), on all host cores:
+    ray-iterations/s, the unit the rays' rate is built from."""
+    import oracle
+    onet = oracle.OracleNet(mlp)
+    t0 = time.perf_counter()
+    r = oracle.cast_rays(onet, o[:nrays], d[:nrays], "fixed", delta=1e-4, t_max=10.0, sigma0=1.0,
+                         max_iters=iters)
+    dt = time.perf_counter() - t0
+    n_it = int(np.sum(r["iters"]))
+    return {"value": n_it / dt, "unit": "ray-iterations/s", "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{nrays} central camera rays of the 39(PE)-[512]x6-1 ELU net, affine-fixed FP64, "
+                      f"{iters} iterations each at most ({n_it} in all), {dt:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -986,6 +1002,10 @@ def main():
                                args.cpu_sample_1core)
         except Exception as e:  # noqa: BLE001 - reported, not fatal
             cpu = {"value": None, "error": str(e)[:200]}
+        try:
+            cpu_rays = cpu_baseline_rays(mlp_ray, o[sel].astype(np.float64), d[sel].astype(np.float64))
+        except Exception as e:  # noqa: BLE001 - reported, not fatal
+            cpu_rays = {"value": None, "error": str(e)[:200]}
         line = {
             "metric": "box-bound evals/s", "value": value, "unit": "box-bound evals/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1020,7 +1040,8 @@ def main():
                      "flop_per_iter": it_flop, "forms": ray_forms, "completion_sample": completion,
                      "same_outcome_frac": float(agree.mean()),
                      "bf16_vs_fp32_iters_per_s": ray_forms["bf16"]["ray_iters_per_s"]
-                     / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30)},
+                     / max(ray_forms["fp32"]["ray_iters_per_s"], 1e-30),
+                     "cpu_baseline": cpu_rays},
             "mesh": mesh,
             "empty_spheres": spheres,
             "frustum": frustum,
