@@ -237,7 +237,9 @@ typedef struct {
  * wait). recheck and converge must be 0; FP64 is not batched; otherwise
  * SRA_EUNSUPPORTED. Segments must not overlap in frontier_out or leaves_out.
  * Uses stream-ordered scratch of about 2 KB per segment plus one byte per
- * node. Asynchronous. */
+ * node. Asynchronous; its segment tables are copied from host memory, so
+ * on a stream that is being captured into a CUDA graph it returns
+ * SRA_EUNSUPPORTED and enqueues nothing. */
 sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_opts *opts,
                                         int32_t n_nets, const float *root_lo, const float *root_hi,
                                         const sra_node *frontier_in, const sra_batch_seg *segs,
@@ -294,7 +296,8 @@ sra_status sra_cast_rays(const sra_net *net, const sra_opts *opts, const float *
  * NO_HIT, NaN at the iteration cap) and, if not NULL, iters (device
  * int32[height * width]: ray iterations after the hand-over). stats (host
  * int64[4], may be NULL): frustum rounds, frustum boxes bounded, pixels
- * handed to rays, 0. Synchronises once per round. Errors as sra_cast_rays. */
+ * handed to rays, 0. Synchronises once per round. Errors as sra_cast_rays;
+ * SRA_EUNSUPPORTED on a stream that is being captured into a CUDA graph. */
 sra_status sra_cast_frustum(const sra_net *net, const sra_opts *opts, const float *eye, const float *dirs,
                             int32_t width, int32_t height, int32_t grid, float *t_hit, int32_t *iters,
                             int64_t *stats, void *stream);
@@ -307,7 +310,8 @@ sra_status sra_cast_frustum(const sra_net *net, const sra_opts *opts, const floa
  * are written to level_counts (host int64[(depth+1)*3], may be NULL).
  * Synchronises the stream once per level. Errors: SRA_ECAPACITY when the
  * leaves exceed cap (*n_leaves holds the needed count, the first cap are
- * written), SRA_EINVAL, SRA_EUNSUPPORTED, SRA_ENOMEM, SRA_ECUDA. */
+ * written), SRA_EINVAL, SRA_EUNSUPPORTED (also on a stream that is being
+ * captured into a CUDA graph), SRA_ENOMEM, SRA_ECUDA. */
 sra_status sra_extract_leaves(const sra_net *net, const sra_opts *opts, const float *xl,
                               const float *xu, int32_t depth, sra_node *leaves_out,
                               int64_t cap, int64_t *n_leaves, int64_t *level_counts,
@@ -325,7 +329,8 @@ sra_status sra_extract_leaves(const sra_net *net, const sra_opts *opts, const fl
  * tris_out (device float[cap][3][3]) is written in leaf, cell (x fastest),
  * tetrahedron order; *n_tris (host) receives the triangle count. Errors:
  * SRA_ECAPACITY when the count exceeds cap (the first cap are written),
- * SRA_EINVAL, SRA_ENOMEM, SRA_ECUDA. Synchronises the stream once. */
+ * SRA_EINVAL, SRA_ENOMEM, SRA_ECUDA, SRA_EUNSUPPORTED on a stream that is
+ * being captured into a CUDA graph. Synchronises the stream once. */
 sra_status sra_mesh_leaves(const sra_net *net, const float *root_lo, const float *root_hi,
                            const sra_node *leaves, int64_t n_leaves, int32_t sub_levels,
                            float *tris_out, int64_t cap, int64_t *n_tris, void *stream);

@@ -145,6 +145,22 @@ sra_status check_opts(const sra_opts *o) {
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
+// Entry points that upload host-side tables or read counts back to the host
+// between their launches cannot be captured into a CUDA graph (a replay would
+// read host memory the call has since released); they refuse a capturing
+// stream instead of enqueueing work.
+sra_status refuse_capture(void *stream, const char *what) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(as_stream(stream), &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return SRA_OK;
+    }
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(SRA_EUNSUPPORTED, "%s cannot be captured into a CUDA graph: it moves host data between its launches",
+                    what);
+    return SRA_OK;
+}
+
 int num_sms() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -832,6 +848,7 @@ sra_status sra_mesh_leaves(const sra_net *n, const float *root_lo, const float *
     g_err.clear();
     sra_status r = check_net(n);
     if (r) return r;
+    if ((r = refuse_capture(stream, "sra_mesh_leaves"))) return r;
     if (!root_lo || !root_hi || !n_tris) return fail(SRA_EINVAL, "null root / n_tris");
     for (int d = 0; d < 3; ++d)
         if (!(root_hi[d] > root_lo[d])) return fail(SRA_EINVAL, "empty root box on axis %d", d);
@@ -1000,6 +1017,7 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
                                         const sra_batch_seg *segs, int32_t n_segs, sra_node *out,
                                         sra_node *leaves, int64_t *counts, void *stream) {
     g_err.clear();
+    if (sra_status rc = refuse_capture(stream, "sra_classify_and_split_batch")) return rc;
     if (!nets || !opts || n_nets < 1 || !segs || n_segs < 1 || !root_lo || !root_hi || !counts)
         return fail(SRA_EINVAL, "null or empty nets / opts / segs / root / counts");
     for (int d = 0; d < 3; ++d)
@@ -1339,6 +1357,7 @@ sra_status sra_cast_frustum(const sra_net *n, const sra_opts *o, const float *ey
     g_err.clear();
     sra_status r = check_net(n);
     if (r) return r;
+    if ((r = refuse_capture(stream, "sra_cast_frustum"))) return r;
     if ((r = check_opts(o))) return r;
     if (!eye || !dirs || !t_hit) return fail(SRA_EINVAL, "null eye / dirs / t_hit");
     if (W < 1 || Hh < 1 || (long long)W * Hh > INT32_MAX || grid < 1 || grid > 4096)
@@ -1462,6 +1481,7 @@ sra_status sra_extract_leaves(const sra_net *n, const sra_opts *o, const float *
     g_err.clear();
     sra_status r = check_net(n);
     if (r) return r;
+    if ((r = refuse_capture(stream, "sra_extract_leaves"))) return r;
     if ((r = check_opts(o))) return r;
     if (!xl || !xu || !n_leaves) return fail(SRA_EINVAL, "null xl/xu/n_leaves");
     if (cap < 0 || (cap > 0 && !leaves)) return fail(SRA_EINVAL, "bad leaves buffer");

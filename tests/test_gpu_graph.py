@@ -1,10 +1,11 @@
 """The asynchronous entry points inside captured CUDA graphs.
 
 sra_bound_boxes, sra_classify_and_split and sra_cast_rays only enqueue work
-on the caller's stream: kernels, memsets and stream-ordered scratch. They can
-therefore be captured into a CUDA graph and replayed with new inputs written
-into the same buffers. A replay must give the same results, bit for bit, as
-an eager call on the same inputs.
+on the caller's stream: kernels, memsets and stream-ordered scratch. They
+can therefore be captured into a CUDA graph and replayed with new inputs
+written into the same buffers. A replay must give the same results, bit for
+bit, as an eager call on the same inputs. The entry points that move host
+data between their launches refuse a capturing stream.
 """
 import numpy as np
 import pytest
@@ -92,9 +93,43 @@ def test_classify_and_split_graph_replay(sra):
     net.close()
 
 
-def test_cast_rays_graph_replay(sra):
+def test_capture_refused_where_host_data_moves(sra):
+    """sra_classify_and_split_batch uploads its segment tables from host
+    memory, and sra_extract_leaves its root and its per-level counts, between
+    their launches: inside a stream capture they return SRA_EUNSUPPORTED and
+    enqueue nothing (a replay would read host memory the call has released).
+    Outside a capture they run as usual."""
     net = sra.Net(wl.net_small_relu())
-    opts = sra.make_opts(arith="fixed", delta=1e-3)
+    opts = sra.make_opts(arith="truncate", K=16)
+    fr = sra.nodes_to_tensor(wl.random_nodes(64, level=3, seed=1))
+    out = torch.empty((8 * 64, 4), dtype=torch.int16, device="cuda")
+    leaves = torch.empty((64, 4), dtype=torch.int16, device="cuda")
+    segs = [dict(net=0, max_level=5, first=0, n=64, out_first=0, cap_out=8 * 64, leaf_first=0, cap_leaves=64)]
+    codes = []
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for call in (lambda: sra.classify_and_split_batch([net], [opts], fr, segs, out, leaves),
+                     lambda: sra.extract_leaves(net, 3, opts=opts)):
+            try:
+                call()
+                codes.append(0)
+            except sra.SraError as e:
+                codes.append(e.code)
+    torch.cuda.synchronize()
+    assert codes == [sra.EUNSUPPORTED, sra.EUNSUPPORTED]
+    counts = sra.classify_and_split_batch([net], [opts], fr, segs, out, leaves)
+    lv, lc = sra.extract_leaves(net, 3, opts=opts)
+    torch.cuda.synchronize()
+    assert int(counts[0, sra.CNT_POSITIVE] + counts[0, sra.CNT_NEGATIVE] + counts[0, sra.CNT_UNKNOWN]) == 64
+    net.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_sound"])
+def test_cast_rays_graph_replay(sra, precision):
+    mlp = wl.net_small_relu() if precision == "fp32" else wl.make_mlp([128] * 3, "elu", seed=35, pe_octaves=2)
+    net = sra.Net(mlp)
+    opts = sra.make_opts(arith="fixed", delta=1e-3, precision=precision, max_iters=3000)
     n = 300
     o = torch.empty((n, 3), device="cuda")
     d = torch.empty((n, 3), device="cuda")
