@@ -68,7 +68,7 @@ def ray_iter_flops(mlp):
 # 1 pass, NVTX range timed_steps): reported only while the kernel's sources
 # are the ones captured (their SHA-1), else null.
 TRAFFIC = {
-    "tc_bound_kernel<256,true,ReLU>": {"sha1": "7416bf556b4edfe805fbc55df0e60cb176f7a40e", "bytes": 3286016,
+    "tc_bound_kernel<256,true,ReLU>": {"sha1": "e26c3f47f915e507ec9f4b60ba07049751ddb429", "bytes": 2964992,
                                        "capture": "profiles/tc_bound_kernel_bf16_sound_relu256x8_truncate64.md"},
 }
 TC_BOUND_SOURCES = ("paper_2202_02444_gb300/csrc/tc_bound.cu", "paper_2202_02444_gb300/csrc/tc_bound_impl.cuh",
@@ -324,12 +324,13 @@ def batched_phase(sra, torch, cap):
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
     # the same 64 trees with BF16-sound bounds on the tensor cores for every
-    # network that has that kernel (one width 128, 256 or 512; K = 16, 32 or
-    # 64), the others in their autotuned FP32 form, all in the same batched
-    # rounds
+    # network that has that kernel (one width 128, 256 or 512; K = 16, 32, 64,
+    # or 128 below width 512), the others in their autotuned FP32 form, all in
+    # the same batched rounds
     tc = [tc_box_net(m) for m in mlps]
-    # the tensor-core kernel's K: the autotuned one where it has a kernel for it (16, 32, 64), else 64
-    k_tc = [r["K"] if r["K"] in (16, 32, 64) else 64 for r in tuned]
+    # the tensor-core kernel's K: the autotuned one where it has a kernel for it, else 64
+    k_tc = [r["K"] if r["K"] in (16, 32, 64) or (r["K"] == 128 and m.widths[1] <= 256) else 64
+            for r, m in zip(tuned, mlps)]
     opts_tc = [sra.make_opts(arith="truncate", K=kt, precision="bf16_sound") if t else o
                for t, o, kt in zip(tc, opts, k_tc)]
     torch.cuda.synchronize()
@@ -461,7 +462,7 @@ def tc_widths_phase(sra, torch, dev, timed):
                          "unknown_frac": float((cl == 0).float().mean())}
         if H == 256:  # the other kept-symbol counts of the kernel
             row["bf16_sound_by_K"] = {}
-            for K in (16, 32):
+            for K in (16, 32, 128):
                 o = sra.make_opts(arith="truncate", K=K, precision="bf16_sound")
                 ms, (lo, hi, cl) = timed(lambda: sra.bound_boxes(net, C_, H_, opts=o))
                 sra.sync_status(net)

@@ -82,8 +82,8 @@ enum { SRA_SLOPE_CHEBYSHEV = 0, SRA_SLOPE_MINRANGE = 1 };
  *               rounding of the noise columns).
  * BF16_SOUND and BF16 serve 3 -> H x L -> 1 networks whose hidden layers are
  * all ReLU, all ELU or all sin (H = 128, 256 or 512, up to 12 hidden layers) with
- * affine-truncate K = 16, 32 or 64 and the Chebyshev slope; other shapes and options
- * return SRA_EUNSUPPORTED. */
+ * affine-truncate K = 16, 32, 64 or (H = 128 or 256) 128 and the Chebyshev slope;
+ * other shapes and options return SRA_EUNSUPPORTED. */
 enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2, SRA_PREC_BF16 = 3 };
 
 /* Tree refinement: 8-way octree (one level = 3 k-d levels on a cube) or the
@@ -231,7 +231,8 @@ typedef struct {
  * int64[n_segs][SRA_CNT_N], zeroed by the caller (or holding earlier
  * chunks' totals, which are appended after). Precision FP32 (the SIMT
  * launches above) or, for networks with the tensor-core path (3 -> H x L -> 1
- * ReLU, ELU or sin, H = 128, 256 or 512) and affine-truncate K = 16, 32 or 64, SRA_PREC_BF16 /
+ * ReLU, ELU or sin, H = 128, 256 or 512) and affine-truncate K = 16, 32, 64 or (H <= 256) 128,
+ * SRA_PREC_BF16 /
  * SRA_PREC_BF16_SOUND: each such segment runs one tensor-core launch beside
  * the SIMT launches (check sra_sync_status on its network for a timed-out
  * wait). recheck and converge must be 0; FP64 is not batched; otherwise

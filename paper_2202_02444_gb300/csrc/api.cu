@@ -306,12 +306,12 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
                               long long count, unsigned long long *recheck_counter,
                               cudaStream_t st) {
     const bool bf16 = o->precision == SRA_PREC_BF16_SOUND || o->precision == SRA_PREC_BF16;
-    if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || !tc_kt_served(o->K) ||
+    if (bf16 && (!n->tc_ok || o->arith != SRA_ARITH_AFFINE_TRUNCATE || !tc_kt_served(o->K, n->tc_H) ||
                  o->slope != SRA_SLOPE_CHEBYSHEV))
         return fail(SRA_EUNSUPPORTED,
                     "BF16 tensor-core bounds need a 3 -> H x L -> 1 network with one activation (ReLU, ELU or sin; "
-                    "H = 128, 256 or 512, at most %d hidden tensor-core layers) with affine-truncate K = 16, 32 or "
-                    "64 and the Chebyshev slope",
+                    "H = 128, 256 or 512, at most %d hidden tensor-core layers) with affine-truncate K = 16, 32, "
+                    "64 or (H <= 256) 128 and the Chebyshev slope",
                     kMaxTcLayers);
     const bool fp64 = o->precision == SRA_PREC_FP64;
     const bool recheck = o->recheck && !fp64;
@@ -326,7 +326,7 @@ sra_status bound_with_recheck(const sra_net *n, const sra_opts *o, BoxSrc src, B
     }
     sra_status r = SRA_OK;
     if (bf16) {
-        const int nb = tc_boxes_per_tile(n->tc_H);
+        const int nb = tc_boxes_per_tile(n->tc_H, o->K);
         const long long tiles = (count + nb - 1) / nb;
         long long grid = num_sms();
         if (grid > tiles) grid = tiles;
@@ -1031,11 +1031,11 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
             return fail(SRA_EUNSUPPORTED,
                         "batched rounds run in FP32 or BF16 without re-check or convergence test (opts[%d])", k);
         if ((pr == SRA_PREC_BF16 || pr == SRA_PREC_BF16_SOUND) &&
-            (!nets[k]->tc_ok || opts[k].arith != SRA_ARITH_AFFINE_TRUNCATE || !tc_kt_served(opts[k].K) ||
+            (!nets[k]->tc_ok || opts[k].arith != SRA_ARITH_AFFINE_TRUNCATE || !tc_kt_served(opts[k].K, nets[k]->tc_H) ||
              opts[k].slope != SRA_SLOPE_CHEBYSHEV))
             return fail(SRA_EUNSUPPORTED,
                         "batched BF16 segments need a network with the tensor-core path and affine-truncate K = 16, "
-                        "32 or 64 (opts[%d])", k);
+                        "32, 64 or (H <= 256) 128 (opts[%d])", k);
     }
     cudaStream_t st = as_stream(stream);
     unsigned char n3[kMaxKdLevels][3], axis[kMaxKdLevels];
@@ -1163,11 +1163,11 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
                  BoundOut bo;
                  memset(&bo, 0, sizeof bo);
                  bo.cls = ds[s].out.cls;
-                 const int nb = tc_boxes_per_tile(n->tc_H);
+                 const sra_opts &so = opts[segs[s].net];
+                 const int nb = tc_boxes_per_tile(n->tc_H, so.K);
                  const long long tiles = (segs[s].n + nb - 1) / nb;
                  long long grid = num_sms();
                  if (grid > tiles) grid = tiles;
-                 const sra_opts &so = opts[segs[s].net];
                  cudaError_t e = launch_tc_bound(n->tc_H, so.K, so.precision == SRA_PREC_BF16_SOUND, n->tcp,
                                                  ds[s].src, bo, (int)grid, ls);
                  if (e != cudaSuccess)

@@ -1,8 +1,8 @@
 // BF16-sound RangeBound on the tensor cores (tcgen05 + TMEM + TMA).
 //
 // Network shape served: 3 -> H -> ... -> H -> 1 ReLU, ELU or sin MLP (H = 128,
-// 256 or 512), affine-truncate with K = 16, 32 or 64 kept noise symbols
-// (Sec. 3.3; one instantiation file per K), the
+// 256 or 512), affine-truncate with K = 16, 32, 64 or (H <= 256) 128 kept
+// noise symbols (Sec. 3.3; one instantiation file per K), the
 // dense layers of App. A Table "affine_update_rules" on tensor cores. One
 // persistent CTA per SM runs the whole network for a tile of NB boxes with
 // NB x H threads (NB = 2 for H <= 256, 1 for H = 512): thread group g (H
@@ -38,23 +38,26 @@ extern template cudaError_t launch_tc_bound_kt<32>(int, bool, const TcParams &, 
                                                    int, cudaStream_t);
 extern template cudaError_t launch_tc_bound_kt<16>(int, bool, const TcParams &, const BoxSrc &, const BoundOut &,
                                                    int, cudaStream_t);
+extern template cudaError_t launch_tc_bound_kt<128>(int, bool, const TcParams &, const BoxSrc &, const BoundOut &,
+                                                    int, cudaStream_t);
 
 int tc_smem_bytes(int H) {
-    return H == 512   ? tc::Layout<512, 64, tc::boxes_per_tile(512)>::ALLOC
-           : H == 256 ? tc::Layout<256, 64, tc::boxes_per_tile(256)>::ALLOC
-           : H == 128 ? tc::Layout<128, 64, tc::boxes_per_tile(128)>::ALLOC
+    return H == 512   ? tc::Layout<512, 64, tc::boxes_per_tile(512, 64)>::ALLOC
+           : H == 256 ? tc::Layout<256, 64, tc::boxes_per_tile(256, 64)>::ALLOC
+           : H == 128 ? tc::Layout<128, 64, tc::boxes_per_tile(128, 64)>::ALLOC
                       : 0;
 }
 
-int tc_boxes_per_tile(int H) { return tc::boxes_per_tile(H); }
+int tc_boxes_per_tile(int H, int K) { return tc::boxes_per_tile(H, K); }
 
-bool tc_kt_served(int K) { return K == 16 || K == 32 || K == 64; }
+bool tc_kt_served(int K, int H) { return K == 16 || K == 32 || K == 64 || (K == 128 && H <= 256); }
 
 cudaError_t launch_tc_bound(int H, int K, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out,
                             int grid, cudaStream_t st) {
     if (K == 64) return launch_tc_bound_kt<64>(H, sound, p, src, out, grid, st);
     if (K == 32) return launch_tc_bound_kt<32>(H, sound, p, src, out, grid, st);
     if (K == 16) return launch_tc_bound_kt<16>(H, sound, p, src, out, grid, st);
+    if (K == 128) return launch_tc_bound_kt<128>(H, sound, p, src, out, grid, st);
     return cudaErrorInvalidValue;
 }
 

@@ -28,9 +28,9 @@ struct TcParams {
 };
 
 int tc_smem_bytes(int H);
-int tc_boxes_per_tile(int H);  // boxes one CTA bounds at a time
-bool tc_kt_served(int K);      // kept-symbol counts with a kernel: 16, 32, 64
-// K kept noise symbols (16, 32 or 64), width H (128, 256 or 512)
+int tc_boxes_per_tile(int H, int K);  // boxes one CTA bounds at a time
+bool tc_kt_served(int K, int H);      // kept-symbol counts with a kernel: 16, 32, 64; 128 for H <= 256
+// K kept noise symbols (16, 32, 64, or 128 for H <= 256), width H (128, 256 or 512)
 cudaError_t launch_tc_bound(int H, int K, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out,
                             int grid, cudaStream_t st);
 template <int KT>

@@ -18,9 +18,11 @@ constexpr int NCC = 16;      // center-chunk columns (MMA N)
 constexpr int NPART = 4;     // partial sums per output-layer dot product
 constexpr uint32_t kSpin = 1u << 22;
 
-// Boxes per tile (one thread group of H threads each) for width H: two at
-// H = 128 and 256, one at H = 512 (two would need 576 TMEM columns).
-constexpr int boxes_per_tile(int H) { return H == 512 ? 1 : 2; }
+// Boxes per tile (one thread group of H threads each) for width H and KT
+// kept symbols: two at H = 128 and 256 with KT <= 64, else one (two boxes
+// at H = 512, or with KT = 128, would need an MMA N or TMEM columns past
+// the limits: N <= 256, 512 columns).
+constexpr int boxes_per_tile(int H, int KT) { return (H == 512 || KT > 64) ? 1 : 2; }
 
 template <int H, int KT, int NBV> struct Layout {
     // KT kept noise symbols per box (16, 32 or 64)
@@ -30,9 +32,9 @@ template <int H, int KT, int NBV> struct Layout {
     static constexpr int MT = H / 128;   // M tiles per layer
     static constexpr int S = H / 64;     // K slices per layer
     // TMEM columns per M tile: NA noise then NCC center accumulators
-    static constexpr int TM_STRIDE = NB == 1 ? 128 : 256;
+    static constexpr int TM_STRIDE = (NB == 1 && NA + NCC <= 128) ? 128 : 256;
     static constexpr int TMEM_COLS = MT * TM_STRIDE <= 256 ? 256 : 512;  // allocated (a power of two)
-    static constexpr int UPS = NB == 1 ? 2 : 1;  // ring units per K slice
+    static constexpr int UPS = (NB == 1 && MT >= 2) ? 2 : 1;  // ring units per K slice
     static constexpr int MPU = MT / UPS;          // M tiles per ring unit
     static constexpr int TILE = 128 * 128;                  // bytes of one 128 x 64 bf16 tile
     static constexpr int STAGE = 2 * MPU * TILE;            // W_b and W_r tiles of one unit
@@ -161,18 +163,36 @@ __device__ void select_topk(const Ctx &x, int Ncur) {
     }
     uint32_t T = 0u;
     {
-        uint32_t nz = 0u, m1 = 0u, m2 = 0u;  // the lane's two largest keys
+        // the lane's two largest keys (four for KT = 128)
+        uint32_t nz = 0u, m1 = 0u, m2 = 0u, m3 = 0u, m4 = 0u;
 #pragma unroll
         for (int k = 0; k < NCH; ++k) {
             nz += key[k] != 0u ? 1u : 0u;
             const uint32_t v = key[k];
-            m2 = v > m1 ? m1 : (v > m2 ? v : m2);
-            m1 = v > m1 ? v : m1;
+            if constexpr (KT > 64) {
+                if (v > m4) {
+                    if (v > m3) {
+                        m4 = m3;
+                        if (v > m2) {
+                            m3 = m2;
+                            if (v > m1) { m2 = m1; m1 = v; } else m2 = v;
+                        } else {
+                            m3 = v;
+                        }
+                    } else {
+                        m4 = v;
+                    }
+                }
+            } else {
+                m2 = v > m1 ? m1 : (v > m2 ? v : m2);
+                m1 = v > m1 ? v : m1;
+            }
         }
         if (__reduce_add_sync(0xffffffffu, nz) > (uint32_t)KT) {
             // T is the largest key with at least KT keys >= T. Every lane holds
-            // two keys >= its m2, so 64 >= KT keys are >= lo; no key exceeds hi.
-            uint32_t lo = __reduce_min_sync(0xffffffffu, m2), hi = __reduce_max_sync(0xffffffffu, m1);
+            // two (four) keys >= its m2 (m4), so 64 >= KT (128 = KT) keys are
+            // >= lo; no key exceeds hi.
+            uint32_t lo = __reduce_min_sync(0xffffffffu, KT > 64 ? m4 : m2), hi = __reduce_max_sync(0xffffffffu, m1);
             while (lo < hi) {  // invariant: count(>= lo) >= KT, count(> hi) < KT
                 const uint32_t w = hi - lo;  // split (lo, hi] at three points
                 const uint32_t c1 = lo + (w + 3u) / 4u, c2 = lo + (2u * w + 3u) / 4u, c3 = lo + (3u * w + 3u) / 4u;
@@ -526,6 +546,165 @@ __device__ void hidden_epilogue(const Ctx &x, const TcParams &p, uint32_t tl, in
     store_neuron<H, SOUND, KT, NBV>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
 }
 
+// Epilogue of one hidden layer with K = 128 kept symbols: the steps of
+// hidden_epilogue over the box's 128 noise columns in two halves of 64 (a
+// thread cannot hold both halves' accumulators): the range sums over both
+// halves (each rounded up), then per half the scaled columns' L1 norms; the
+// selection over the 128 + H candidates; then per half the dropped
+// magnitudes and the write-back of the kept columns, whose positions
+// continue from the first half into the second. Each half is read from TMEM
+// again where it is needed.
+template <int H, bool SOUND, int ACT, int NBV>
+__device__ void hidden_epilogue_wide(const Ctx &x, const TcParams &p, uint32_t tl, int col0, uint32_t ccol,
+                                     float bias, float xacc) {
+    constexpr int KT = 128;
+    using Lt = Layout<H, KT, NBV>;
+    const int g = x.g, lane = x.lane, wg = x.wg;
+    float *score = (float *)(x.smem + Lt::SC_OFF) + g * Lt::NCAND;
+    float *part = (float *)(x.smem + Lt::PART_OFF) + g * (H / 32) * KT;
+    const int quad = lane >> 2, qi = lane & 3;
+    float cc[2], a[2][8][4];
+    auto load_half = [&](int hf) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            ptx::tmem_ld16x256_x8(tl + ((uint32_t)(16 * h) << 16) + (uint32_t)(col0 + 64 * hf), &a[h][0][0]);
+        ptx::tmem_wait_ld();
+    };
+    ptx::tmem_ld2(ccol, cc);
+    load_half(0);
+    const float c_n = (cc[0] + cc[1]) + bias;
+    float xinf_n;
+    if (SOUND) {
+        xinf_n = ru_mul(xacc, p.kappa);
+        xinf_n = ru_fma(ru_add(2.f * fabsf(c_n), fabsf(bias)), 1.1920929e-07f, xinf_n);
+    } else {
+        xinf_n = xacc;
+    }
+    const int nq = 32 * wg + 16 * (qi >> 1) + 8 * (qi & 1) + quad;
+    const float cq = __shfl_sync(0xffffffffu, c_n, nq & 31);
+    const float xq = __shfl_sync(0xffffffffu, xinf_n, nq & 31);
+    float sa;
+    {
+        float ps[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int hf = 0; hf < 2; ++hf) {
+            if (hf == 1) load_half(1);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int h = s >> 1, q0 = 2 * (s & 1);
+                float t[16];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    t[2 * j] = fabsf(a[h][j][q0]);
+                    t[2 * j + 1] = fabsf(a[h][j][q0 + 1]);
+                }
+                ps[s] = ru_add(ps[s], ru_sum<16>(t));
+            }
+        }
+        sa = quad_scatter_ru(ps, qi);
+    }
+    float al, ga, c2, xi;
+    act_rule<SOUND, ACT>(sa, cq, xq, p.ub2u, al, ga, c2, xi);
+    score[KT + nq] = ga;
+    float als[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) als[s] = __shfl_sync(0xffffffffu, al, (lane & ~3) | s);
+    auto scale = [&]() {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[0][j][q] *= als[q >> 1];
+                a[1][j][q] *= als[2 + (q >> 1)];
+            }
+    };
+    // column L1 norms of each half (the reduce-scatter of hidden_epilogue):
+    // half 1 first, which the range sums left in the registers; half 0 then
+    // stays there, scaled, for the write-back below
+#pragma unroll 1
+    for (int hf = 1; hf >= 0; --hf) {
+        if (hf == 0) load_half(0);
+        scale();
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                v[2 * j + e] = (fabsf(a[0][j][e]) + fabsf(a[0][j][2 + e])) + (fabsf(a[1][j][e]) + fabsf(a[1][j][2 + e]));
+#pragma unroll
+        for (int half = 8, o = 16; o >= 4; half >>= 1, o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int k = 0; k < half; ++k) {
+                const float send = up ? v[k] : v[k + half];
+                const float keepv = up ? v[k + half] : v[k];
+                v[k] = keepv + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        part[wg * KT + 64 * hf + 8 * quad + 2 * qi] = v[0];
+        part[wg * KT + 64 * hf + 8 * quad + 2 * qi + 1] = v[1];
+    }
+    group_sync(g, H);
+    select_topk<H, KT, NBV>(x, KT);
+    group_sync(g, H);
+    const uint32_t *kmw = (const uint32_t *)(x.smem + Lt::KM_OFF) + g * Lt::KMW;
+    const int mi = lane >> 3, r = lane & 7;
+    const int nb = 32 * wg + 8 * mi;
+    const uint32_t xa = ptx::smem_u32(x.smem + Lt::XA_OFF + (nb >> 6) * Lt::XA_SLICE);
+    const uint32_t c16 = (uint32_t)((nb & 63) >> 3);
+    const uint32_t dummy = ptx::smem_u32(x.smem + Lt::DUMMY_OFF) + 16u * (uint32_t)lane;
+    const uint32_t below_r = (1u << r) - 1u;
+    uint32_t pre = 0u;  // kept old columns below the current byte, over both halves
+#pragma unroll 1
+    for (int hf = 0; hf < 2; ++hf) {
+        if (hf == 1) {
+            load_half(1);
+            scale();
+        }
+        const unsigned long long kept = ((unsigned long long)kmw[2 * hf + 1] << 32) | kmw[2 * hf];
+        {
+            const unsigned long long mine = ~kept >> (2 * qi);
+            float mf[16];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int e = 0; e < 2; ++e) mf[2 * j + e] = ((mine >> (8 * j + e)) & 1ull) ? 1.f : 0.f;
+            float pd[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int h = s >> 1, q0 = 2 * (s & 1);
+                float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    d0 = ru_fma(mf[2 * j], fabsf(a[h][j][q0]), d0);
+                    d1 = ru_fma(mf[2 * j + 1], fabsf(a[h][j][q0 + 1]), d1);
+                }
+                pd[s] = ru_add(d0, d1);
+            }
+            xi = ru_add(xi, quad_scatter_ru(pd, qi));
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t byte = (uint32_t)(kept >> (8 * j)) & 0xffu;
+            const bool k = (byte >> r) & 1u;
+            const uint32_t row = (uint32_t)(g * KT) + pre + (uint32_t)__popc(byte & below_r);
+            pre += (uint32_t)__popc(byte);
+            const bool in = idx_ok((long long)row - g * KT, KT, x.status, 104);
+            const uint32_t addr = (k && in) ? xa + row * 128u + ((c16 ^ (row & 7u)) << 4) : dummy;
+            uint32_t R[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const __nv_bfloat162 b = __floats2bfloat162_rn(a[m >> 1][j][2 * (m & 1)], a[m >> 1][j][2 * (m & 1) + 1]);
+                R[m] = *(const uint32_t *)&b;
+            }
+            ptx::stmatrix_x4_trans(addr, R[0], R[1], R[2], R[3]);
+        }
+    }
+    if (!cand_kept<H, KT, NBV>(x, KT + nq)) xi = ru_add(xi, ga);
+    fill_new_rows<H, SOUND, KT, NBV>(x, KT);
+    store_neuron<H, SOUND, KT, NBV>(x, p, nq, c2, xi, SOUND ? operand_mag_bound(al, sa, ga) : 0.f);
+}
+
 template <int H, bool SOUND, int ACT, int KT, int NBV>
 __global__ void __launch_bounds__(Layout<H, KT, NBV>::NT, 1) tc_bound_kernel(const __grid_constant__ TcParams p, BoxSrc src,
                                                                     BoundOut out) {
@@ -782,8 +961,14 @@ __global__ void __launch_bounds__(Layout<H, KT, NBV>::NT, 1) tc_bound_kernel(con
             if (__syncthreads_or(*x.abort_flag != 0)) break;  // every operand read of this layer is done
             // ---- epilogue of the group's box -------------------------------
             const float xacc = NB == 2 ? ru_add(xown, ((const float *)(x.smem + Lt::XP_OFF))[g * H + i]) : xown;
-            hidden_epilogue<H, SOUND, ACT, KT, NBV>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
-                                           tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias, xacc);
+            if constexpr (KT > 64)
+                hidden_epilogue_wide<H, SOUND, ACT, NBV>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
+                                                         tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias,
+                                                         xacc);
+            else
+                hidden_epilogue<H, SOUND, ACT, KT, NBV>(x, p, tl, m_of_thread * TM_STRIDE + g * KT,
+                                                        tl + (uint32_t)(m_of_thread * TM_STRIDE + NA + 2 * g), bias,
+                                                        xacc);
         }
         if (__syncthreads_or(*x.abort_flag != 0)) break;
         // ---- output layer (H -> 1) on the SIMT cores ------------------------------
@@ -910,7 +1095,7 @@ __global__ void __launch_bounds__(Layout<H, KT, NBV>::NT, 1) tc_bound_kernel(con
 // form and the activation rule for one kept-symbol count KT.
 template <int H, bool SOUND, int ACT, int KT>
 static cudaError_t launch_one(const TcParams &p, const BoxSrc &src, const BoundOut &out, int grid, cudaStream_t st) {
-    constexpr int NBV = tc::boxes_per_tile(H);
+    constexpr int NBV = tc::boxes_per_tile(H, KT);
     using Lt = tc::Layout<H, KT, NBV>;
     const int smem = Lt::ALLOC;
     cudaError_t e = cudaFuncSetAttribute(tc::tc_bound_kernel<H, SOUND, ACT, KT, NBV>,
@@ -941,7 +1126,10 @@ static cudaError_t launch_h(bool sound, const TcParams &p, const BoxSrc &src, co
 template <int KT>
 cudaError_t launch_tc_bound_kt(int H, bool sound, const TcParams &p, const BoxSrc &src, const BoundOut &out,
                                int grid, cudaStream_t st) {
-    if (H == 512) return launch_h<512, KT>(sound, p, src, out, grid, st);
+    if (H == 512) {
+        if constexpr (KT <= 64) return launch_h<512, KT>(sound, p, src, out, grid, st);
+        else return cudaErrorInvalidValue;  // 4 M tiles x (128 + 16) columns exceed TMEM
+    }
     if (H == 256) return launch_h<256, KT>(sound, p, src, out, grid, st);
     if (H == 128) return launch_h<128, KT>(sound, p, src, out, grid, st);
     return cudaErrorInvalidValue;

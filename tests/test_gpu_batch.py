@@ -139,6 +139,7 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
         (wl.make_mlp([512] * 4, "elu", seed=47), dict(arith="truncate", K=64, precision="bf16"), 3, 64, 6),
         (wl.make_mlp([256] * 4, "relu", seed=48), dict(arith="truncate", K=16, precision="bf16_sound"), 4, 700, 7),
         (wl.make_mlp([128] * 5, "sin", seed=49), dict(arith="truncate", K=32, precision="bf16"), 4, 333, 7),
+        (wl.make_mlp([256] * 3, "elu", seed=50), dict(arith="truncate", K=128, precision="bf16_sound"), 4, 257, 6),
     ]
     nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
     try:
@@ -163,7 +164,7 @@ def test_batch_rejects_unserved_bf16(sra):
         out = torch.empty((80, 4), dtype=torch.int16, device="cuda")
         seg = [dict(net=0, max_level=5, n=10, cap_out=80, cap_leaves=0)]
         for n, o in ((net, sra.make_opts(arith="truncate", K=64, precision="bf16_sound")),
-                     (net2, sra.make_opts(arith="truncate", K=48, precision="bf16_sound")),  # K in {16, 32, 64}
+                     (net2, sra.make_opts(arith="truncate", K=48, precision="bf16_sound")),  # K in {16, 32, 64, 128}
                      (net2, sra.make_opts(arith="truncate", K=64, precision="fp64")),
                      (net2, sra.make_opts(arith="truncate", K=64, precision="bf16", recheck=True))):
             with pytest.raises(sra.SraError) as e:

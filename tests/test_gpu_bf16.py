@@ -72,12 +72,12 @@ def test_bf16_sound_contains_samples(sra, name):
 
 
 KT_CASES = [("relu256x8", 16), ("relu256x8", 32), ("sin256x3", 16), ("elu128x4", 32), ("relu512x4", 16),
-            ("elu512x3", 32)]
+            ("elu512x3", 32), ("relu256x8", 128), ("sin256x3", 128), ("elu128x4", 128)]
 
 
 @pytest.mark.parametrize("name,K", KT_CASES)
 def test_bf16_kept_symbols(sra, name, K):
-    """The tensor-core kernel with K = 16 or 32 kept symbols (Sec. 3.3
+    """The tensor-core kernel with K = 16, 32 or 128 kept symbols (Sec. 3.3
     truncate). BF16-sound: every sampled value of f lies inside [lo, hi]
     (no tolerance) and the range contains the oracle's affine-truncate-K
     range (selection near-ties exempt). Plain BF16: radius within 2 % of the
@@ -108,11 +108,11 @@ def test_bf16_kept_symbols(sra, name, K):
 EDGE_NETS = {"relu128x4": NETS["relu128x4"], "relu256x8": NETS["relu256x8"], "relu512x4": NETS["relu512x4"]}
 
 
-@pytest.mark.parametrize("name", list(EDGE_NETS))
+@pytest.mark.parametrize("name,K", [(n, 64) for n in EDGE_NETS] + [("relu256x8", 128)])
 @pytest.mark.parametrize("precision", ["bf16_sound", "bf16"])
-def test_bf16_batch_sizes(sra, name, precision):
+def test_bf16_batch_sizes(sra, name, K, precision):
     """Ragged and degenerate batch sizes around the tile (two boxes at H <=
-    256, one at H = 512) and the persistent grid (one CTA per SM): a batch of
+    256 with K <= 64, else one) and the persistent grid (one CTA per SM): a batch of
     n boxes gives, bit for bit, what the first n boxes of a 400-box batch
     give (a box's result depends only on its own data and its slot in the
     tile, and the slots of the first n boxes are the same in both); n = 0
@@ -120,10 +120,10 @@ def test_bf16_batch_sizes(sra, name, precision):
     mlp = EDGE_NETS[name]()
     net = sra.Net(mlp)
     c, h = level_boxes(400, seed=13)
-    big = run(sra, net, c, h, arith="truncate", K=64, precision=precision)
+    big = run(sra, net, c, h, arith="truncate", K=K, precision=precision)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     for n in sorted({0, 1, 2, 3, sms - 1, sms, sms + 1, 2 * sms + 1, 399}):
-        small = run(sra, net, c[:n], h[:n], arith="truncate", K=64, precision=precision)
+        small = run(sra, net, c[:n], h[:n], arith="truncate", K=K, precision=precision)
         for a, b in zip(small, big):
             assert np.array_equal(a, b[:n]), (name, n)
     net.close()
@@ -167,10 +167,10 @@ SHALLOW = {"relu128x3": lambda: wl.make_mlp([128] * 3, "relu", seed=31),
 SHALLOW_BOXES = {"sin128x3": (1 / 1024, 1 / 128), "sin256x3": (1 / 4096, 1 / 256)}
 
 
-SHALLOW_K = {"relu256x3": 32, "elu128x3": 16}  # more kept-symbol counts than K = 64
+SHALLOW_K = [("relu256x3", 32), ("elu128x3", 16), ("relu256x3", 128), ("sin128x3", 128)]  # K other than 64
 
 
-@pytest.mark.parametrize("name,K", [(n, 64) for n in SHALLOW] + list(SHALLOW_K.items()))
+@pytest.mark.parametrize("name,K", [(n, 64) for n in SHALLOW] + SHALLOW_K)
 def test_bf16_sound_classes_on_shallow_nets(sra, name, K):
     """Where the |W| amplification of the a-priori rounding radius is small
     (two tensor-core layers), the sound form decides nearly everything the
@@ -238,8 +238,13 @@ def test_bf16_unsupported_shapes(sra):
     with pytest.raises(sra.SraError) as e:  # the kernel's rules use the Chebyshev slope
         sra.bound_boxes(net, c, c, arith="truncate", K=64, slope="minrange", precision="bf16_sound")
     assert e.value.code == sra.EUNSUPPORTED
-    with pytest.raises(sra.SraError) as e:  # kernels for K = 16, 32 and 64 only
+    with pytest.raises(sra.SraError) as e:  # kernels for K = 16, 32, 64 and 128 only
         sra.bound_boxes(net, c, c, arith="truncate", K=48, precision="bf16")
+    assert e.value.code == sra.EUNSUPPORTED
+    net.close()
+    net = sra.Net(NETS["relu512x4"]())
+    with pytest.raises(sra.SraError) as e:  # K = 128 at width 512 would need 576 TMEM columns
+        sra.bound_boxes(net, c, c, arith="truncate", K=128, precision="bf16_sound")
     assert e.value.code == sra.EUNSUPPORTED
     net.close()
     mixed = wl.make_mlp([128] * 3, "relu", seed=2)
