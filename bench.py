@@ -209,13 +209,22 @@ def serving_nets():
          for k in range(4)]
 
 
+# Resident networks (indices into serving_nets()) whose depth-9 leaf set, in
+# affine-truncate K=16 FP32, fits the 2^20-node leaf buffer of a leaf job:
+# 65k-900k leaves each. The sin networks of the uneven generator and the
+# positional-encoding ELU networks leave nearly every cell UNKNOWN (more than
+# 2^20 leaves by depth 7), so a leaf job on them can only end in SRA_ECAPACITY.
+SERVING_LEAF_NETS = (3, 4, 6, 8, 9, 11)
+
+
 def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
     """Poisson request traces (seed 5) against 16 resident networks through
     sra_serve: a third each of 64x64 ray tiles (cap 200 iterations per ray),
-    batches of U[256, 65536] boxes and leaf-extraction jobs to depth 9 (frontier
-    capacity 2^20 nodes per level). Each ray or box request takes the
-    BF16-sound form (tensor cores) with probability 1/2 where its network has
-    that kernel, else FP32.
+    batches of U[256, 65536] boxes and leaf-extraction jobs to depth 9 (leaf
+    and per-level frontier buffers of 2^20 nodes; the job walks levels that
+    are wider in chunks) on the networks of SERVING_LEAF_NETS. Each ray or
+    box request takes the BF16-sound form (tensor cores) with probability
+    1/2 where its network has that kernel, else FP32.
     Returns p50 / p99 latency (arrival to completion) and throughput per rate."""
     mlps = serving_nets()
     nets = [sra.Net(m) for m in mlps]
@@ -235,7 +244,9 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
                        "39(PE)-[512]x6-1, seeds 2..5); Poisson arrivals (seed 5); 1/3 each: 64x64 "
                        "camera ray tile (affine-fixed, delta 1e-3, cap 200 iterations), U[256,65536] "
                        "boxes (affine-truncate K=16 FP32 / K=64 BF16-sound), leaf extraction to depth 9 "
-                       "(K=16, frontier cap 2^20 per level); BF16-sound form (rays and boxes) for half "
+                       "(K=16 FP32, 2^20-node leaf and per-level frontier buffers, wider levels walked in "
+                       "chunks) on the 6 uneven nets whose depth-9 leaves fit 2^20 "
+                       f"(indices {list(SERVING_LEAF_NETS)}); BF16-sound form (rays and boxes) for half "
                        "the requests whose net has that kernel",
            "slots": slots, "frontier_budget_bytes": budget, "rates": []}
     for lam in rates:
@@ -266,6 +277,7 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
                 leaves = torch.empty((1 << 20, 4), dtype=torch.int16, device=dev)
                 keep.append(leaves)
                 form = 1
+                j = SERVING_LEAF_NETS[j % len(SERVING_LEAF_NETS)]
                 reqs.append(sra.leaf_request(j, form, arrivals[i], 9, leaves))
             meta.append((kind, form))
         torch.cuda.synchronize()
@@ -289,6 +301,7 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
             "ok": int((st == 0).sum()), "capacity_exceeded": int((st == 5).sum()),
             "other_errors": int(((st != 0) & (st != 5)).sum()),
             "max_concurrent_slots_used": len({r.slot for r in res if r.slot >= 0}),
+            "leaves_per_leaf_job": [int(r.n_out) for r, m in zip(res, meta) if m[0] == 2],
             "by": per})
         del keep
     for n in nets:
@@ -591,8 +604,6 @@ def run_reference(args):
     mlp = wl.net_relu256x8()
     K = 64
     rng = np.random.default_rng(1)
-    # the frontier comes from the CPU: level-7 nodes of the oracle's own tree
-    # are too costly to enumerate; a seeded level-7 sample stands in
     # the GPU arm's frontier needs the network's own level-6 tree, which the
     # oracle cannot build in minutes; uniformly drawn level-7 nodes cost the
     # same per box (the bound's work does not depend on where the box is)

@@ -406,19 +406,28 @@ sra_status sra_sync_status(const sra_net *net, void *stream);
  * served, each into a free slot (one CUDA stream per slot) when the device
  * memory it reserves fits in the frontier budget, and drives every admitted
  * request on its slot's stream while others run, so the work of several
- * requests overlaps on the device. A leaf job is stepped one octree level at
- * a time (Proc. 3); between its levels the loop serves other slots.
+ * requests overlaps on the device. A leaf job (Proc. 3) is stepped one chunk
+ * of one level's frontier at a time; between its chunks the loop serves
+ * other slots. It walks the tree depth-first over chunks: the next chunk is
+ * always the front of the deepest level that still has unprocessed nodes,
+ * at most cap / 8 nodes (cap / 2 for the k-d split), so every level's
+ * frontier fits a buffer of cap nodes however large the tree grows.
  *
  * Memory: the loop allocates one device arena of cfg->frontier_bytes and
  * one stream per slot when it starts and frees them before it returns. A
- * leaf job takes its two frontier buffers (2 * cap * sizeof(sra_node)) and
- * its counters from the arena; ray and box requests reserve their
- * stream-ordered scratch size (16 bytes per ray / box) from the same budget.
- * A request whose reservation exceeds the whole budget ends at once with
- * SRA_ENOMEM.
+ * leaf job takes one frontier buffer per level 0..depth
+ * ((depth + 1) * cap * sizeof(sra_node), each rounded up to 256 bytes) and
+ * its counters from the arena, fixed for the job's lifetime; ray and box
+ * requests reserve their stream-ordered scratch size (16 bytes per ray /
+ * box) from the same budget. A request whose reservation exceeds the whole
+ * budget ends at once with SRA_ENOMEM.
  *
  * Results are the same as a lone call of the entry point each kind uses
- * (sra_cast_rays, sra_bound_boxes, sra_classify_and_split level by level).
+ * (sra_cast_rays, sra_bound_boxes, sra_extract_leaves): a leaf job's leaves
+ * come out in the order of a level-by-level build, because chunks are taken
+ * from the front of their level. (With opts->converge the converged leaves
+ * of shallower levels are the same set, but they interleave with deeper
+ * leaves in the order the chunks ran.)
  */
 enum { SRA_REQ_RAYS = 0, SRA_REQ_BOXES = 1, SRA_REQ_LEAVES = 2 };
 
@@ -436,12 +445,16 @@ typedef struct {
     int32_t *iters;        /* RAYS: iterations per ray (device int32[n]; may be NULL) */
     uint8_t *cls;          /* BOXES: classes (device uint8[n]; may be NULL) */
     sra_node *leaves;      /* LEAVES: UNKNOWN nodes at `depth` (device sra_node[cap]) */
-    int64_t cap;           /* LEAVES: capacity of leaves and of each frontier level */
+    int64_t cap;           /* LEAVES: capacity of leaves and of each level's frontier
+                              buffer (the chunk size is cap / 8, octree) */
     /* written by sra_serve */
-    int64_t n_out;         /* LEAVES: leaves found (or children needed on overflow) */
+    int64_t n_out;         /* LEAVES: leaves found. On SRA_ECAPACITY: the leaves found
+                              when the job stopped (more than cap; the tree may hold
+                              more), or, if cap is below the fan-out, the children of
+                              one node */
     int32_t status;        /* sra_status of this request */
     int32_t slot;          /* slot that ran it (-1: never admitted) */
-    int32_t levels;        /* LEAVES: levels completed */
+    int32_t levels;        /* LEAVES: levels reached (deepest level with nodes + 1) */
     int32_t pad;
     double t_admit, t_done;/* seconds after the trace starts */
 } sra_request;

@@ -7,13 +7,24 @@
 // and their device-memory reservation fits in an arena of fixed size (the
 // frontier budget). An admitted request is a short state machine on its
 // slot's stream: a ray tile or a box batch is one call of the entry point it
-// uses; a leaf job (Proc. 3) is one sra_classify_and_split call per octree
-// level, with the level's counters copied to pinned memory behind an event.
-// The loop polls the events; a finished step either ends the request or
-// launches its next level, so the device always holds work of several
-// requests at once and a long leaf job never blocks the others between its
-// levels. Frontier buffers of leaf jobs live in the arena and stay on the
-// device for the job's lifetime.
+// uses; a leaf job (Proc. 3) is a sequence of sra_classify_and_split calls,
+// each over a chunk of one level's frontier, with the chunk's counters copied
+// to pinned memory behind an event. The loop polls the events; a finished
+// step either ends the request or launches its next chunk, so the device
+// always holds work of several requests at once and a long leaf job never
+// blocks the others between its chunks.
+//
+// A leaf job walks its tree depth-first over chunks, so its frontier memory
+// is fixed by its capacity and depth, whatever the size of the tree: one
+// buffer of `cap` nodes per level. The next chunk always comes from the
+// deepest level that still has unprocessed nodes, taken from the front of
+// that level, at most cap / fanout nodes (fanout 8 for the octree, 2 for the
+// k-d split), so its children fit the next level's buffer, which is empty at
+// that point. Taking chunks from the front keeps the level-by-level order:
+// the descendants of earlier nodes of a level come first at every deeper
+// level, so the leaves come out in the order of a breadth-first build
+// (sra_extract_leaves). The buffers live in the arena and stay on the device
+// for the job's lifetime.
 #include <chrono>
 #include <cstring>
 #include <deque>
@@ -25,6 +36,8 @@
 
 namespace sra {
 namespace {
+
+constexpr int kMaxServeDepth = 15;
 
 // First-fit allocator over one device buffer; host-side bookkeeping only.
 // Blocks are 256-byte aligned; freed blocks merge with free neighbours.
@@ -77,17 +90,25 @@ struct Slot {
     int64_t *hcounts = nullptr;  // pinned, SRA_CNT_N entries
     int64_t req = -1;            // active request, -1 = free
     size_t off = 0, bytes = 0;   // arena reservation
-    // leaf job state
-    int level = 0;
-    long long ncur = 0;
-    int64_t leaves_found = 0;  // leaves of earlier levels (convergence test)
-    sra_node *bufA = nullptr, *bufB = nullptr;
+    // leaf job state: one frontier buffer per level 0..depth, with the
+    // level's node count and the read position of its next chunk
+    sra_node *levels = nullptr;
+    size_t level_bytes = 0;
+    int level = 0;        // level of the chunk in flight
+    int64_t chunk = 0;    // nodes in the chunk in flight
+    int64_t n[kMaxServeDepth + 1] = {}, next[kMaxServeDepth + 1] = {};
+    int deepest = 0;      // deepest level reached
+    int64_t leaves_found = 0;
     int64_t *dcounts = nullptr;
+    sra_node *buf(int l) const { return (sra_node *)((char *)levels + (size_t)l * level_bytes); }
 };
 
+size_t level_buffer_bytes(const sra_request &q) {
+    return Arena::round((size_t)(q.cap > 0 ? q.cap : 1) * sizeof(sra_node));
+}
+
 size_t reservation(const sra_request &q) {
-    if (q.kind == SRA_REQ_LEAVES)
-        return 2 * Arena::round((size_t)(q.cap > 0 ? q.cap : 1) * sizeof(sra_node)) + 256;
+    if (q.kind == SRA_REQ_LEAVES) return (size_t)(q.depth + 1) * level_buffer_bytes(q) + 256;
     return (size_t)(q.n > 0 ? q.n : 1) * 16;
 }
 
@@ -115,7 +136,7 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
             return set_error(SRA_EINVAL, "request %lld: kind %d", (long long)i, q.kind);
         if (i > 0 && q.arrival < reqs[i - 1].arrival)
             return set_error(SRA_EINVAL, "request %lld arrives before request %lld", (long long)i, (long long)i - 1);
-        if (q.kind == SRA_REQ_LEAVES && (q.depth < 0 || q.depth > 15 || q.cap < 1 || !q.leaves))
+        if (q.kind == SRA_REQ_LEAVES && (q.depth < 0 || q.depth > kMaxServeDepth || q.cap < 1 || !q.leaves))
             return set_error(SRA_EINVAL, "request %lld: leaf job needs 0 <= depth <= 15, cap >= 1, leaves", (long long)i);
     }
     for (int64_t i = 0; i < n_req; ++i) {
@@ -174,16 +195,23 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
         s.req = -1;
         ++ended;
     };
-    // Enqueue the next level of a leaf job: classify and split the current
-    // frontier, copy the level's counters to pinned memory, record the event.
-    auto launch_level = [&](Slot &s) -> sra_status {
+    // Enqueue the next chunk of a leaf job (from the front of level s.level):
+    // classify and split it into the (empty) buffer of the next level, copy
+    // the chunk's counters to pinned memory, record the event.
+    auto launch_chunk = [&](Slot &s) -> sra_status {
         const sra_request &q = reqs[s.req];
+        const sra_opts &o = forms[q.form];
+        const int64_t fan = o.split == SRA_SPLIT_OCTREE ? 8 : 2;
+        const int l = s.level;
+        const int64_t room = q.cap / fan > 0 ? q.cap / fan : 1;
+        s.chunk = s.n[l] - s.next[l] < room ? s.n[l] - s.next[l] : room;
         if (cudaMemsetAsync(s.dcounts, 0, SRA_CNT_N * sizeof(int64_t), s.st) != cudaSuccess)
             return SRA_ECUDA;
         const int64_t lcap = q.cap > s.leaves_found ? q.cap - s.leaves_found : 0;
-        sra_status r = sra_classify_and_split(nets[q.net], &forms[q.form], kRootLo, kRootHi, s.bufA, s.ncur,
-                                              q.depth, s.bufB, q.cap, lcap > 0 ? q.leaves + s.leaves_found : nullptr,
-                                              lcap, s.dcounts, s.st);
+        const bool last = l == q.depth;
+        sra_status r = sra_classify_and_split(nets[q.net], &o, kRootLo, kRootHi, s.buf(l) + s.next[l], s.chunk,
+                                              q.depth, last ? nullptr : s.buf(l + 1), last ? 0 : q.cap,
+                                              lcap > 0 ? q.leaves + s.leaves_found : nullptr, lcap, s.dcounts, s.st);
         if (r) return r;
         if (cudaMemcpyAsync(s.hcounts, s.dcounts, SRA_CNT_N * sizeof(int64_t), cudaMemcpyDeviceToHost, s.st) !=
                 cudaSuccess ||
@@ -206,22 +234,21 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
         } else if (q.kind == SRA_REQ_BOXES) {
             r = sra_bound_boxes(net, o, q.a, q.b, q.n, q.lo, q.hi, q.cls, s.st);
         } else {
-            char *base = (char *)arena_mem + off;
-            const size_t buf = Arena::round((size_t)q.cap * sizeof(sra_node));
-            s.bufA = (sra_node *)base;
-            s.bufB = (sra_node *)(base + buf);
-            s.dcounts = (int64_t *)(base + 2 * buf);
-            s.level = 0;
-            s.ncur = 1;
+            s.levels = (sra_node *)((char *)arena_mem + off);
+            s.level_bytes = level_buffer_bytes(q);
+            s.dcounts = (int64_t *)((char *)arena_mem + off + (size_t)(q.depth + 1) * s.level_bytes);
+            for (int l = 0; l <= kMaxServeDepth; ++l) s.n[l] = s.next[l] = 0;
+            s.level = s.deepest = 0;
+            s.n[0] = 1;
             s.leaves_found = 0;
             // the root node (level 0, index 0) is all zero bytes
-            r = cudaMemsetAsync(s.bufA, 0, sizeof(sra_node), s.st) == cudaSuccess ? SRA_OK : SRA_ECUDA;
-            if (!r) r = launch_level(s);
+            r = cudaMemsetAsync(s.buf(0), 0, sizeof(sra_node), s.st) == cudaSuccess ? SRA_OK : SRA_ECUDA;
+            if (!r) r = launch_chunk(s);
         }
         if (!r && q.kind != SRA_REQ_LEAVES && cudaEventRecord(s.ev, s.st) != cudaSuccess) r = SRA_ECUDA;
         if (r) finish(s, r);
     };
-    // A finished step: end the request or launch the leaf job's next level.
+    // A finished step: end the request or launch the leaf job's next chunk.
     auto advance = [&](Slot &s) {
         sra_request &q = reqs[s.req];
         if (q.kind != SRA_REQ_LEAVES) {
@@ -229,28 +256,36 @@ extern "C" sra_status sra_serve(const sra_net *const *nets, int32_t n_nets, cons
             return;
         }
         const int64_t *hc = s.hcounts;
-        q.levels = s.level + 1;
+        const int l = s.level;
+        s.next[l] += s.chunk;
         s.leaves_found += hc[SRA_CNT_LEAVES];
-        if (s.level == q.depth) {
+        if (s.leaves_found > q.cap) {  // the leaves do not fit: stop (n_out is a lower bound)
             q.n_out = s.leaves_found;
-            finish(s, q.n_out > q.cap ? SRA_ECAPACITY : SRA_OK);
-            return;
-        }
-        const long long children = hc[SRA_CNT_CHILDREN];
-        if (children > q.cap) {  // the next level does not fit the job's frontier buffers
-            q.n_out = children;
             finish(s, SRA_ECAPACITY);
             return;
         }
-        if (children == 0) {
+        if (l < q.depth) {
+            const int64_t children = hc[SRA_CNT_CHILDREN];
+            if (children > q.cap) {  // only when cap < fanout: one node's children do not fit
+                q.n_out = children;
+                finish(s, SRA_ECAPACITY);
+                return;
+            }
+            s.n[l + 1] = children;
+            s.next[l + 1] = 0;
+            if (children > 0 && l + 1 > s.deepest) s.deepest = l + 1;
+        }
+        q.levels = s.deepest + 1;
+        // the deepest level with unprocessed nodes
+        int d = l < q.depth ? l + 1 : l;
+        while (d >= 0 && s.next[d] >= s.n[d]) --d;
+        if (d < 0) {
             q.n_out = s.leaves_found;
-            finish(s, q.n_out > q.cap ? SRA_ECAPACITY : SRA_OK);
+            finish(s, SRA_OK);
             return;
         }
-        std::swap(s.bufA, s.bufB);
-        s.ncur = children;
-        s.level += 1;
-        sra_status r = launch_level(s);
+        s.level = d;
+        sra_status r = launch_chunk(s);
         if (r) finish(s, r);
     };
 

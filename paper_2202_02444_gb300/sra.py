@@ -389,7 +389,8 @@ def box_request(net, form, arrival, centers, halfw, lo, hi, cls=None):
 
 def leaf_request(net, form, arrival, depth, leaves):
     """A leaf-extraction job (Proc. 3 to `depth`) for serve(); leaves is a
-    CUDA int16 [cap, 4] tensor that also sets the frontier capacity."""
+    CUDA int16 [cap, 4] tensor that also sets the capacity of each level's
+    frontier buffer (the job reserves depth + 1 of them)."""
     return Request(kind=REQ_LEAVES, net=net, form=form, arrival=float(arrival), depth=int(depth),
                    leaves=_ptr(leaves), cap=leaves.shape[0])
 

@@ -118,7 +118,7 @@ def test_admission_by_frontier_memory(sra, nets):
     """A budget that holds one leaf job at a time: leaf jobs never overlap."""
     fo = forms(sra)
     cap = 1 << 14
-    per_job = 2 * (((cap * 8) + 255) // 256 * 256) + 256
+    per_job = (4 + 1) * (((cap * 8) + 255) // 256 * 256) + 256  # one buffer per level 0..4
     reqs, keep = [], []
     for i in range(3):
         leaves = torch.empty((cap, 4), dtype=torch.int16, device="cuda")
@@ -129,6 +129,38 @@ def test_admission_by_frontier_memory(sra, nets):
     spans = sorted((r.t_admit, r.t_done) for r in out)
     for k in range(len(spans) - 1):
         assert spans[k + 1][0] >= spans[k][1]
+
+
+@pytest.mark.parametrize("net_i,depth,split", [(0, 6, "octree"), (1, 5, "octree"), (0, 15, "kd")])
+def test_leaf_job_levels_larger_than_its_buffers(sra, nets, net_i, depth, split):
+    """A leaf job whose tree has levels larger than its per-level buffers
+    walks them in chunks, depth-first, and still returns the leaves of a
+    level-by-level build in the same order."""
+    fo = forms(sra) + [sra.make_opts(arith="truncate", K=16, split=split)]
+    form = len(fo) - 1
+    ref, lc = sra.extract_leaves(nets[net_i], depth, opts=fo[form])
+    n = ref.shape[0]
+    widest = int(lc.sum(axis=1).max())
+    cap = max(n, 64)
+    assert widest > cap, (widest, cap)  # a level-by-level job with this cap overflows
+    leaves = torch.full((cap, 4), -1, dtype=torch.int16, device="cuda")
+    req = sra.leaf_request(net_i, form, 0.0, depth, leaves)
+    out = sra.serve(nets, fo, [req], slots=1, frontier_bytes=64 << 20, realtime=False)
+    assert out[0].status == 0, out[0].status
+    assert out[0].n_out == n and out[0].levels == depth + 1
+    assert same(leaves[:n], ref)
+
+
+def test_leaf_job_stops_when_its_leaves_overflow(sra, nets):
+    fo = forms(sra)
+    ref, _ = sra.extract_leaves(nets[0], 6, opts=fo[1])
+    cap = ref.shape[0] // 3
+    leaves = torch.full((cap, 4), -1, dtype=torch.int16, device="cuda")
+    out = sra.serve(nets, fo, [sra.leaf_request(0, 1, 0.0, 6, leaves)], slots=1,
+                    frontier_bytes=64 << 20, realtime=False)
+    assert out[0].status == sra.ECAPACITY
+    assert cap < out[0].n_out <= ref.shape[0]
+    assert same(leaves, ref[:cap])  # the first cap leaves, in order
 
 
 def test_request_failures_stay_local(sra, nets):
