@@ -238,9 +238,13 @@ typedef struct {
  * wait). recheck and converge must be 0; FP64 is not batched; otherwise
  * SRA_EUNSUPPORTED. Segments must not overlap in frontier_out or leaves_out.
  * Uses stream-ordered scratch of about 2 KB per segment plus one byte per
- * node. Asynchronous; its segment tables are copied from host memory, so
- * on a stream that is being captured into a CUDA graph it returns
- * SRA_EUNSUPPORTED and enqueues nothing. */
+ * node. Asynchronous. The segment tables reach the device as kernel
+ * parameters (no host memory is read after the call returns), so the round
+ * can be captured into a CUDA graph and replayed with new nodes written into
+ * the same buffers, for the same segments; counts must be zeroed inside the
+ * graph if each replay should start from zero. The library's pool of
+ * streams is created by the first batched call that runs more than one
+ * launch: make one eager call with the same segments before a capture. */
 sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_opts *opts,
                                         int32_t n_nets, const float *root_lo, const float *root_hi,
                                         const sra_node *frontier_in, const sra_batch_seg *segs,

@@ -145,10 +145,34 @@ sra_status check_opts(const sra_opts *o) {
 
 cudaStream_t as_stream(void *s) { return (cudaStream_t)s; }
 
-// Entry points that upload host-side tables or read counts back to the host
-// between their launches cannot be captured into a CUDA graph (a replay would
-// read host memory the call has since released); they refuse a capturing
-// stream instead of enqueueing work.
+// Host tables to device memory through kernel parameters: one launch of
+// upload_kernel carries up to kUploadChunk bytes by value, so the copy reads
+// no host memory after the launch is enqueued, and a CUDA graph that captures
+// it holds the bytes itself. (A captured cudaMemcpyAsync from host memory
+// reads that memory again at every replay, after the call has released it.)
+constexpr int kUploadChunk = 4000;  // with the other two parameters, under 4 KB of parameters
+struct UploadChunk {
+    unsigned char b[kUploadChunk];
+};
+__global__ void upload_kernel(const __grid_constant__ UploadChunk c, unsigned char *dst, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = c.b[k];
+}
+cudaError_t upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+    UploadChunk c = {};
+    for (size_t off = 0; off < bytes; off += kUploadChunk) {
+        const int n = (int)(bytes - off < (size_t)kUploadChunk ? bytes - off : (size_t)kUploadChunk);
+        memcpy(c.b, (const unsigned char *)src + off, (size_t)n);
+        upload_kernel<<<1, 256, 0, st>>>(c, (unsigned char *)dst + off, n);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Entry points that read counts back to the host between their launches
+// cannot be captured into a CUDA graph (a replay would not repeat the host
+// decisions taken on them); they refuse a capturing stream instead of
+// enqueueing work.
 sra_status refuse_capture(void *stream, const char *what) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(as_stream(stream), &cs) != cudaSuccess) {
@@ -1017,7 +1041,6 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
                                         const sra_batch_seg *segs, int32_t n_segs, sra_node *out,
                                         sra_node *leaves, int64_t *counts, void *stream) {
     g_err.clear();
-    if (sra_status rc = refuse_capture(stream, "sra_classify_and_split_batch")) return rc;
     if (!nets || !opts || n_nets < 1 || !segs || n_segs < 1 || !root_lo || !root_hi || !counts)
         return fail(SRA_EINVAL, "null or empty nets / opts / segs / root / counts");
     for (int d = 0; d < 3; ++d)
@@ -1144,12 +1167,12 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
     int *ordd = (int *)(base + b_cls + b_blk + b_ds + b_ss);
     unsigned long long *next = (unsigned long long *)(base + b_cls + b_blk + b_ds + b_ss + b_ord);
     for (int s = 0; s < n_segs; ++s) ds[s].out.cls = cls + segs[s].first;
-    SRA_CK(cudaMemcpyAsync(dsd, ds.data(), ds.size() * sizeof(BatchSegDev), cudaMemcpyHostToDevice, st));
-    SRA_CK(cudaMemcpyAsync(ssd, ss.data(), ss.size() * sizeof(BatchSplitSeg), cudaMemcpyHostToDevice, st));
-    if (!order.empty())
-        SRA_CK(cudaMemcpyAsync(ordd, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // the segment tables travel as kernel parameters (no host memory is read
+    // after these calls return, so the round can be captured into a graph)
+    SRA_CK(upload(dsd, ds.data(), ds.size() * sizeof(BatchSegDev), st));
+    SRA_CK(upload(ssd, ss.data(), ss.size() * sizeof(BatchSplitSeg), st));
+    if (!order.empty()) SRA_CK(upload(ordd, order.data(), order.size() * sizeof(int), st));
     SRA_CK(cudaMemsetAsync(next, 0, launches.size() * 8 + 8, st));
-    // the host arrays are copied before these calls return (pageable sources)
     // heaviest launch first: the lighter ones fill the SMs its tail frees
     std::vector<size_t> lorder(launches.size());
     for (size_t k = 0; k < lorder.size(); ++k) lorder[k] = k;

@@ -1,11 +1,13 @@
 """The asynchronous entry points inside captured CUDA graphs.
 
-sra_bound_boxes, sra_classify_and_split and sra_cast_rays only enqueue work
-on the caller's stream: kernels, memsets and stream-ordered scratch. They
-can therefore be captured into a CUDA graph and replayed with new inputs
-written into the same buffers. A replay must give the same results, bit for
-bit, as an eager call on the same inputs. The entry points that move host
-data between their launches refuse a capturing stream.
+sra_bound_boxes, sra_classify_and_split, sra_classify_and_split_batch and
+sra_cast_rays only enqueue work on the caller's stream: kernels (the batched
+round's segment tables travel as kernel parameters), memsets and
+stream-ordered scratch. They can therefore be captured into a CUDA graph and
+replayed with new inputs written into the same buffers. A replay must give
+the same results, bit for bit, as an eager call on the same inputs. The
+entry points that read counts back to the host between their launches
+refuse a capturing stream.
 """
 import numpy as np
 import pytest
@@ -94,35 +96,74 @@ def test_classify_and_split_graph_replay(sra):
 
 
 def test_capture_refused_where_host_data_moves(sra):
-    """sra_classify_and_split_batch uploads its segment tables from host
-    memory, and sra_extract_leaves its root and its per-level counts, between
-    their launches: inside a stream capture they return SRA_EUNSUPPORTED and
-    enqueue nothing (a replay would read host memory the call has released).
-    Outside a capture they run as usual."""
+    """sra_extract_leaves reads each level's counts back to the host before
+    it launches the next level: inside a stream capture it returns
+    SRA_EUNSUPPORTED and enqueues nothing. Outside a capture it runs as
+    usual."""
     net = sra.Net(wl.net_small_relu())
     opts = sra.make_opts(arith="truncate", K=16)
-    fr = sra.nodes_to_tensor(wl.random_nodes(64, level=3, seed=1))
-    out = torch.empty((8 * 64, 4), dtype=torch.int16, device="cuda")
-    leaves = torch.empty((64, 4), dtype=torch.int16, device="cuda")
-    segs = [dict(net=0, max_level=5, first=0, n=64, out_first=0, cap_out=8 * 64, leaf_first=0, cap_leaves=64)]
     codes = []
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g):
-        for call in (lambda: sra.classify_and_split_batch([net], [opts], fr, segs, out, leaves),
-                     lambda: sra.extract_leaves(net, 3, opts=opts)):
-            try:
-                call()
-                codes.append(0)
-            except sra.SraError as e:
-                codes.append(e.code)
+        try:
+            sra.extract_leaves(net, 3, opts=opts)
+            codes.append(0)
+        except sra.SraError as e:
+            codes.append(e.code)
     torch.cuda.synchronize()
-    assert codes == [sra.EUNSUPPORTED, sra.EUNSUPPORTED]
-    counts = sra.classify_and_split_batch([net], [opts], fr, segs, out, leaves)
+    assert codes == [sra.EUNSUPPORTED]
     lv, lc = sra.extract_leaves(net, 3, opts=opts)
     torch.cuda.synchronize()
-    assert int(counts[0, sra.CNT_POSITIVE] + counts[0, sra.CNT_NEGATIVE] + counts[0, sra.CNT_UNKNOWN]) == 64
+    assert int(lc.sum()) > 0
     net.close()
+
+
+def test_batch_round_graph_replay(sra):
+    """The batched round over two networks (an FP32 SIMT segment beside a
+    BF16-sound tensor-core one), captured into a graph and replayed on new
+    frontier nodes in the same buffers, gives what an eager round gives on
+    those nodes, bit for bit: classes, children, leaves and counters."""
+    nets = [sra.Net(wl.net_small_relu()), sra.Net(wl.make_mlp([128] * 3, "relu", seed=50))]
+    opts = [sra.make_opts(arith="truncate", K=16),
+            sra.make_opts(arith="truncate", K=16, precision="bf16_sound")]
+    n0, n1 = 300, 200
+    segs = [dict(net=0, max_level=6, first=0, n=n0, out_first=0, cap_out=8 * n0, leaf_first=0, cap_leaves=n0),
+            dict(net=1, max_level=5, first=n0, n=n1, out_first=8 * n0, cap_out=8 * n1, leaf_first=n0,
+                 cap_leaves=n1)]
+
+    def nodes(seed):
+        return sra.nodes_to_tensor(np.concatenate([wl.random_nodes(n0, level=5, seed=seed),
+                                                   wl.random_nodes(n1, level=4, seed=seed + 100)]))
+
+    fr = torch.empty((n0 + n1, 4), dtype=torch.int16, device="cuda")
+    out = torch.empty((8 * (n0 + n1), 4), dtype=torch.int16, device="cuda")
+    leaves = torch.empty((n0 + n1, 4), dtype=torch.int16, device="cuda")
+    counts = torch.zeros((2, sra.CNT_N), dtype=torch.int64, device="cuda")
+    fr.copy_(nodes(1))
+
+    def round_():
+        counts.zero_()
+        out.fill_(-1)
+        leaves.fill_(-1)
+        sra.classify_and_split_batch(nets, opts, fr, segs, out, leaves, counts=counts)
+
+    g = capture(round_)
+    for seed in (2, 3):
+        fr.copy_(nodes(seed))
+        g.replay()
+        torch.cuda.synchronize()
+        got = (counts.clone(), out.clone(), leaves.clone())
+        out2 = torch.full_like(out, -1)
+        leaves2 = torch.full_like(leaves, -1)
+        cnt2 = sra.classify_and_split_batch(nets, opts, fr, segs, out2, leaves2)
+        torch.cuda.synchronize()
+        assert torch.equal(got[0], cnt2)
+        assert torch.equal(got[1], out2) and torch.equal(got[2], leaves2)
+        assert int(cnt2[:, sra.CNT_CHILDREN].sum()) > 0
+    for n in nets:
+        sra.sync_status(n)
+        n.close()
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16_sound"])
