@@ -195,10 +195,11 @@ class ClockSampler:
 
 def tc_box_net(m):
     """The network has the tensor-core bound kernel: a 3 -> H x L -> 1 ReLU,
-    ELU or sin network with one hidden width H in {128, 256, 512} and at most 12
-    hidden tensor-core layers, no positional encoding."""
+    ELU or sin network with one hidden width H in {32, 64, 128, 256, 512}
+    (32 and 64 padded with zeros to 128) and at most 12 hidden tensor-core
+    layers, no positional encoding."""
     return (m.pe_octaves == 0 and m.n_layers >= 3 and m.n_layers - 2 <= 12 and len(set(m.acts)) == 1
-            and m.acts[0] in (1, 2, 3) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (128, 256, 512))
+            and m.acts[0] in (1, 2, 3) and len(set(m.widths[1:-1])) == 1 and m.widths[1] in (32, 64, 128, 256, 512))
 
 
 def serving_nets():
@@ -337,9 +338,9 @@ def batched_phase(sra, torch, cap):
     flop = sum(r["nodes"] * box_flops(m, t["K"]) for r, m, t in zip(res, mlps, tuned))
     same = all(a["levels"] == b["levels"] and a["leaves"] == b["leaves"] for a, b in zip(res, res1))
     # the same 64 trees with BF16-sound bounds on the tensor cores for every
-    # network that has that kernel (one width 128, 256 or 512; K = 16, 32, 64,
-    # or 128 below width 512), the others in their autotuned FP32 form, all in
-    # the same batched rounds
+    # network that has that kernel (one width 32, 64, 128, 256 or 512; K = 16,
+    # 32, 64, or 128 below width 512), the others in their autotuned FP32
+    # form, all in the same batched rounds
     tc = [tc_box_net(m) for m in mlps]
     # the tensor-core kernel's K: the autotuned one where it has a kernel for it, else 64
     k_tc = [r["K"] if r["K"] in (16, 32, 64) or (r["K"] == 128 and m.widths[1] <= 256) else 64
@@ -446,7 +447,8 @@ def policies_phase(sra, torch, dev):
 
 def tc_widths_phase(sra, torch, dev, timed):
     """The tensor-core bound kernel at each width it serves (3-[H]x4-1 ReLU,
-    He init, seed 51; H = 128 and 256 bound two boxes per CTA, H = 512 one),
+    He init, seed 51; H = 64 runs the 128-wide kernel on zero-padded weights;
+    H = 64, 128 and 256 bound two boxes per CTA, H = 512 one),
     affine-truncate K = 64 on 32,768 boxes (half-widths log-U[1/1024, 1/64]),
     against the FP32 SIMT kernel on the same boxes."""
     B = 1 << 15
@@ -455,7 +457,7 @@ def tc_widths_phase(sra, torch, dev, timed):
     peak = measured_peak("bf16_tflops", 1900.0)[0]
     out = {"workload": f"ReLU 3-[H]x4-1 (He init, seed 51), {B} boxes, half-widths log-U[1/1024, 1/64], "
                        "affine-truncate K=64", "peak_tflops": peak, "widths": {}}
-    for H in (128, 256, 512):
+    for H in (64, 128, 256, 512):  # width 64 runs the 128-wide kernel on zero-padded weights
         mlp = wl.make_mlp([H] * 4, "relu", seed=51)
         net = sra.Net(mlp)
         flop = box_flops(mlp, 64)

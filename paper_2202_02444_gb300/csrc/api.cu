@@ -393,51 +393,87 @@ sra_status check_net(const sra_net *n) {
 }
 
 // Prepare the tensor-core path if the network has its shape: 3 inputs,
-// L-1 >= 2 hidden layers of one width H in {128, 256, 512}, all ReLU, all ELU
-// or all sin, scalar output.
+// L-1 >= 2 hidden layers of one width Hn in {32, 64, 128, 256, 512}, all
+// ReLU, all ELU or all sin, scalar output. Widths 32 and 64 run the 128-wide
+// kernel (M = 128 is the kernel's MMA tile) on weights padded with zeros:
+// the padded neurons get exactly zero weights, bias and output weight, so
+// their value and noise entries are 0, their range is [0, 0] and each rule
+// maps it to 0 (a new symbol of magnitude 0, or the rule's padding of it),
+// and the real neurons' sums gain only zero terms. The rounding constants
+// take the padded width, whose sums are the longer ones.
 void prepare_tc(sra_net *n, const float *params) {
-    const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
-    if (n->pe || L < 3 || L - 2 > kMaxTcLayers || (H != 128 && H != 256 && H != 512)) return;
+    const int L = n->L, Hn = n->widths.size() > 1 ? n->widths[1] : 0;
+    if (n->pe || L < 3 || L - 2 > kMaxTcLayers ||
+        (Hn != 32 && Hn != 64 && Hn != 128 && Hn != 256 && Hn != 512))
+        return;
     for (int l = 1; l < L; ++l)
-        if (n->widths[l] != H) return;
+        if (n->widths[l] != Hn) return;
     const int act = n->acts[0];
     if (act != SRA_ACT_RELU && act != SRA_ACT_ELU && act != SRA_ACT_SIN) return;
     for (int l = 0; l + 1 < L; ++l)
         if (n->acts[l] != act) return;
+    const int H = Hn < 128 ? 128 : Hn;  // kernel width
     const int nh = L - 2;
     const size_t per = (size_t)H * H * 2;
-    const size_t bytes = 2 * nh * per + 256;
+    // device layout: W_b, W_r of every hidden layer; the status word (256 B);
+    // then FP32 [H] biases of layers 0 .. L-2, the output weights [H] and the
+    // first layer's weights [H][3], zero past the network's width
+    const size_t off_status = 2 * nh * per, off_bias = off_status + 256;
+    const size_t off_wout = off_bias + (size_t)(L - 1) * H * 4, off_w0 = off_wout + (size_t)H * 4;
+    const size_t bytes = off_w0 + (size_t)H * 3 * 4;
     if (cudaMalloc(&n->tc_buf, bytes) != cudaSuccess) { n->tc_buf = nullptr; cudaGetLastError(); return; }
+    char *dev = (char *)n->tc_buf;
+    auto give_up = [&]() {
+        cudaFree(n->tc_buf);
+        n->tc_buf = nullptr;
+        cudaGetLastError();
+    };
     std::vector<__nv_bfloat16> hi((size_t)H * H), lo((size_t)H * H);
-    size_t off = (size_t)3 * H + H;  // skip layer 0 (W0, b0)
+    std::vector<float> tail((bytes - off_bias) / 4, 0.f);  // biases, output and first-layer weights
+    float *bias = tail.data(), *wout = bias + (size_t)(L - 1) * H, *w0 = wout + H;
+    // layer 0: W0 [Hn][3] row-major, then b0 [Hn]
+    for (int i = 0; i < Hn; ++i)
+        for (int d = 0; d < 3; ++d) w0[i * 3 + d] = params[i * 3 + d];
+    for (int i = 0; i < Hn; ++i) bias[i] = params[3 * Hn + i];
+    size_t off = (size_t)3 * Hn + Hn;
     TcParams &t = n->tcp;
     memset(&t, 0, sizeof t);
     for (int l = 1; l <= nh; ++l) {
-        const float *W = params + off;
-        for (size_t e = 0; e < (size_t)H * H; ++e) {
-            const __nv_bfloat16 h = __float2bfloat16_rn(W[e]);
-            hi[e] = h;
-            lo[e] = __float2bfloat16_rn(W[e] - __bfloat162float(h));
-        }
-        char *dhi = (char *)n->tc_buf + (2 * (l - 1)) * per, *dlo = dhi + per;
+        const float *W = params + off;  // [Hn][Hn] row-major (out x in)
+        std::fill(hi.begin(), hi.end(), __float2bfloat16_rn(0.f));
+        std::fill(lo.begin(), lo.end(), __float2bfloat16_rn(0.f));
+        for (int i = 0; i < Hn; ++i)
+            for (int j = 0; j < Hn; ++j) {
+                const float w = W[(size_t)i * Hn + j];
+                const __nv_bfloat16 h = __float2bfloat16_rn(w);
+                hi[(size_t)i * H + j] = h;
+                lo[(size_t)i * H + j] = __float2bfloat16_rn(w - __bfloat162float(h));
+            }
+        for (int i = 0; i < Hn; ++i) bias[(size_t)l * H + i] = params[off + (size_t)Hn * Hn + i];
+        char *dhi = dev + (2 * (l - 1)) * per, *dlo = dhi + per;
         if (cudaMemcpy(dhi, hi.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(dlo, lo.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
             make_bf16_tile_map(&t.wb[l - 1], dhi, H, H, 128, 64) != 0 ||
             make_bf16_tile_map(&t.wr[l - 1], dlo, H, H, 128, 64) != 0) {
-            cudaFree(n->tc_buf);
-            n->tc_buf = nullptr;
+            give_up();
             return;
         }
-        off += (size_t)H * H + H;
+        off += (size_t)Hn * Hn + Hn;
     }
-    t.W0 = nullptr;  // filled from the FP32 copy below
-    for (int l = 0; l < L; ++l) t.b[l] = n->dev.layer[l].b;
-    t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
-    t.bout = params[off + H];         // the output layer's bias follows its H weights
+    for (int i = 0; i < Hn; ++i) wout[i] = params[off + i];  // output layer [1][Hn], then its bias
+    if (cudaMemcpy(dev + off_bias, tail.data(), tail.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(dev + off_status, 0, sizeof(int)) != cudaSuccess) {
+        give_up();
+        return;
+    }
+    for (int l = 0; l + 1 < L; ++l) t.b[l] = (const float *)(dev + off_bias + (size_t)l * H * 4);
+    t.b[L - 1] = n->dev.layer[L - 1].b;
+    t.W0 = (const float *)(dev + off_w0);
+    t.wout = (const float *)(dev + off_wout);
+    t.bout = params[off + Hn];  // the output layer's bias follows its Hn weights
     t.L = L;
     t.act = act;
-    t.status = (int *)((char *)n->tc_buf + 2 * nh * per);
-    cudaMemset(t.status, 0, sizeof(int));
+    t.status = (int *)(dev + off_status);
     // rounding constants (u = 2^-24, u_b = 2^-8); accumulation model: each
     // 16-deep MMA step adds at most 17 * 2^-23 of the sum of its terms' sizes
     const double u = std::ldexp(1.0, -24), ub = std::ldexp(1.0, -8);
@@ -736,18 +772,6 @@ sra_status sra_load_mlp(const sra_mlp_desc *d, sra_net **out) {
     }
     prepare_tc(n, d->params);
     prepare_tc_rays(n, d->params);
-    if (n->tc_ok) {
-        // layer-0 weights row-major [H][3] for the tensor-core kernel's first layer
-        const size_t w0 = (size_t)n->tc_H * 3 * sizeof(float);
-        void *dw0 = nullptr;
-        if (cudaMalloc(&dw0, w0) == cudaSuccess &&
-            cudaMemcpy(dw0, d->params, w0, cudaMemcpyHostToDevice) == cudaSuccess) {
-            n->tcp.W0 = (const float *)dw0;
-        } else {
-            if (dw0) cudaFree(dw0);
-            n->tc_ok = false;
-        }
-    }
     cudaGetLastError();
     *out = n;
     return SRA_OK;
@@ -758,7 +782,6 @@ sra_status sra_free_mlp(sra_net *n) {
     cudaDeviceSynchronize();
     if (n->buf) cudaFree(n->buf);
     if (n->tc_buf) cudaFree(n->tc_buf);
-    if (n->tcp.W0) cudaFree((void *)n->tcp.W0);
     if (n->tcr_buf) cudaFree(n->tcr_buf);
     delete n;
     return SRA_OK;
