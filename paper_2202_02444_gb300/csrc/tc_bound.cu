@@ -1,8 +1,7 @@
 // BF16-sound RangeBound on the tensor cores (tcgen05 + TMEM + TMA).
 //
 // Network shape served: 3 -> H -> ... -> H -> 1 ReLU, ELU or sin MLP (H = 128,
-// 256 or 512; networks of width 32 or 64 arrive padded with zeros to 128),
-// affine-truncate with K = 16, 32, 64 or (H <= 256) 128 kept
+// 256 or 512), affine-truncate with K = 16, 32, 64 or (H <= 256) 128 kept
 // noise symbols (Sec. 3.3; one instantiation file per K), the
 // dense layers of App. A Table "affine_update_rules" on tensor cores. One
 // persistent CTA per SM runs the whole network for a tile of NB boxes with
