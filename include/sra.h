@@ -80,13 +80,14 @@ enum { SRA_SLOPE_CHEBYSHEV = 0, SRA_SLOPE_MINRANGE = 1 };
  *   BF16:       the same tensor-core computation without the rounding radius
  *               (plain, like FP32; results differ from FP64 by BF16 operand
  *               rounding of the noise columns).
- * BF16_SOUND and BF16 serve 3 -> H x L -> 1 networks whose hidden layers are
- * all ReLU, all ELU or all sin (H = 32, 64, 128, 256 or 512, up to 12 hidden
- * layers) with affine-truncate K = 16, 32, 64 or (H <= 256) 128 and the
- * Chebyshev slope; H = 32 and 64 run the 128-wide kernel on weights padded
- * with zeros (the padded neurons stay exactly zero; their sums count in the
- * rounding radius, as if the network were 128 wide). Other shapes and
- * options return SRA_EUNSUPPORTED. */
+ * BF16_SOUND and BF16 serve networks with 3 inputs (no positional
+ * encoding), 2 to 13 hidden layers of widths up to 512, all ReLU, all ELU or
+ * all sin, and a scalar output, with affine-truncate K = 16, 32, 64 or
+ * (H <= 256) 128 and the Chebyshev slope. The kernel runs at the width
+ * H in {128, 256, 512} that holds every hidden layer; a narrower layer runs
+ * on weights padded with zeros (the padded neurons stay exactly zero; their
+ * sums count in the rounding radius, as if the network were H wide). Other
+ * shapes and options return SRA_EUNSUPPORTED. */
 enum { SRA_PREC_FP32 = 0, SRA_PREC_FP64 = 1, SRA_PREC_BF16_SOUND = 2, SRA_PREC_BF16 = 3 };
 
 /* Tree refinement: 8-way octree (one level = 3 k-d levels on a cube) or the
@@ -234,7 +235,7 @@ typedef struct {
  * int64[n_segs][SRA_CNT_N], zeroed by the caller (or holding earlier
  * chunks' totals, which are appended after). Precision FP32 (the SIMT
  * launches above) or, for networks with the tensor-core path (3 -> H x L -> 1
- * ReLU, ELU or sin, H = 32, 64, 128, 256 or 512) and affine-truncate K = 16, 32, 64 or (H <= 256) 128,
+ * ReLU, ELU or sin, hidden widths up to 512, run at H = 128, 256 or 512) and affine-truncate K = 16, 32, 64 or (H <= 256) 128,
  * SRA_PREC_BF16 /
  * SRA_PREC_BF16_SOUND: each such segment runs one tensor-core launch beside
  * the SIMT launches (check sra_sync_status on its network for a timed-out

@@ -393,31 +393,35 @@ sra_status check_net(const sra_net *n) {
 }
 
 // Prepare the tensor-core path if the network has its shape: 3 inputs,
-// L-1 >= 2 hidden layers of one width Hn in {32, 64, 128, 256, 512}, all
-// ReLU, all ELU or all sin, scalar output. Widths 32 and 64 run the 128-wide
-// kernel (M = 128 is the kernel's MMA tile) on weights padded with zeros:
-// the padded neurons get exactly zero weights, bias and output weight, so
-// their value and noise entries are 0, their range is [0, 0] and each rule
-// maps it to 0 (a new symbol of magnitude 0, or the rule's padding of it),
-// and the real neurons' sums gain only zero terms. The rounding constants
-// take the padded width, whose sums are the longer ones.
+// L-1 >= 2 hidden layers of widths up to 512, all ReLU, all ELU or all sin,
+// scalar output. The kernel runs at one width H in {128, 256, 512}, the
+// smallest that holds every hidden layer (M = 128 is its MMA tile): a network
+// narrower than H somewhere runs on weights padded with zeros. The padded
+// neurons get exactly zero weights, bias and output weight, so their value
+// and noise entries are 0, their range is [0, 0] and each rule maps it to 0
+// (a new symbol of magnitude 0, or the rule's padding of it, which meets
+// only zero weights), and the real neurons' sums gain only zero terms. The
+// rounding constants take the padded width, whose sums are the longer ones.
 void prepare_tc(sra_net *n, const float *params) {
-    const int L = n->L, Hn = n->widths.size() > 1 ? n->widths[1] : 0;
-    if (n->pe || L < 3 || L - 2 > kMaxTcLayers ||
-        (Hn != 32 && Hn != 64 && Hn != 128 && Hn != 256 && Hn != 512))
+    const int L = n->L;
+    if (n->pe || L < 3 || L - 2 > kMaxTcLayers || n->widths.size() != (size_t)L + 1 || n->widths[0] != 3 ||
+        n->widths[L] != 1)
         return;
-    for (int l = 1; l < L; ++l)
-        if (n->widths[l] != Hn) return;
+    int wmax = 0;
+    for (int l = 1; l < L; ++l) {
+        if (n->widths[l] < 1 || n->widths[l] > 512) return;
+        wmax = std::max(wmax, n->widths[l]);
+    }
     const int act = n->acts[0];
     if (act != SRA_ACT_RELU && act != SRA_ACT_ELU && act != SRA_ACT_SIN) return;
     for (int l = 0; l + 1 < L; ++l)
         if (n->acts[l] != act) return;
-    const int H = Hn < 128 ? 128 : Hn;  // kernel width
+    const int H = wmax <= 128 ? 128 : (wmax <= 256 ? 256 : 512);  // kernel width
     const int nh = L - 2;
     const size_t per = (size_t)H * H * 2;
     // device layout: W_b, W_r of every hidden layer; the status word (256 B);
     // then FP32 [H] biases of layers 0 .. L-2, the output weights [H] and the
-    // first layer's weights [H][3], zero past the network's width
+    // first layer's weights [H][3], zero past the network's widths
     const size_t off_status = 2 * nh * per, off_bias = off_status + 256;
     const size_t off_wout = off_bias + (size_t)(L - 1) * H * 4, off_w0 = off_wout + (size_t)H * 4;
     const size_t bytes = off_w0 + (size_t)H * 3 * 4;
@@ -431,25 +435,27 @@ void prepare_tc(sra_net *n, const float *params) {
     std::vector<__nv_bfloat16> hi((size_t)H * H), lo((size_t)H * H);
     std::vector<float> tail((bytes - off_bias) / 4, 0.f);  // biases, output and first-layer weights
     float *bias = tail.data(), *wout = bias + (size_t)(L - 1) * H, *w0 = wout + H;
-    // layer 0: W0 [Hn][3] row-major, then b0 [Hn]
-    for (int i = 0; i < Hn; ++i)
+    // layer 0: W0 [w1][3] row-major, then b0 [w1]
+    const int w1 = n->widths[1];
+    for (int i = 0; i < w1; ++i)
         for (int d = 0; d < 3; ++d) w0[i * 3 + d] = params[i * 3 + d];
-    for (int i = 0; i < Hn; ++i) bias[i] = params[3 * Hn + i];
-    size_t off = (size_t)3 * Hn + Hn;
+    for (int i = 0; i < w1; ++i) bias[i] = params[3 * w1 + i];
+    size_t off = (size_t)3 * w1 + w1;
     TcParams &t = n->tcp;
     memset(&t, 0, sizeof t);
     for (int l = 1; l <= nh; ++l) {
-        const float *W = params + off;  // [Hn][Hn] row-major (out x in)
+        const int in = n->widths[l], out = n->widths[l + 1];
+        const float *W = params + off;  // [out][in] row-major
         std::fill(hi.begin(), hi.end(), __float2bfloat16_rn(0.f));
         std::fill(lo.begin(), lo.end(), __float2bfloat16_rn(0.f));
-        for (int i = 0; i < Hn; ++i)
-            for (int j = 0; j < Hn; ++j) {
-                const float w = W[(size_t)i * Hn + j];
+        for (int i = 0; i < out; ++i)
+            for (int j = 0; j < in; ++j) {
+                const float w = W[(size_t)i * in + j];
                 const __nv_bfloat16 h = __float2bfloat16_rn(w);
                 hi[(size_t)i * H + j] = h;
                 lo[(size_t)i * H + j] = __float2bfloat16_rn(w - __bfloat162float(h));
             }
-        for (int i = 0; i < Hn; ++i) bias[(size_t)l * H + i] = params[off + (size_t)Hn * Hn + i];
+        for (int i = 0; i < out; ++i) bias[(size_t)l * H + i] = params[off + (size_t)out * in + i];
         char *dhi = dev + (2 * (l - 1)) * per, *dlo = dhi + per;
         if (cudaMemcpy(dhi, hi.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(dlo, lo.data(), per, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -458,9 +464,10 @@ void prepare_tc(sra_net *n, const float *params) {
             give_up();
             return;
         }
-        off += (size_t)Hn * Hn + Hn;
+        off += (size_t)out * in + out;
     }
-    for (int i = 0; i < Hn; ++i) wout[i] = params[off + i];  // output layer [1][Hn], then its bias
+    const int wl = n->widths[L - 1];
+    for (int i = 0; i < wl; ++i) wout[i] = params[off + i];  // output layer [1][wl], then its bias
     if (cudaMemcpy(dev + off_bias, tail.data(), tail.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(dev + off_status, 0, sizeof(int)) != cudaSuccess) {
         give_up();
@@ -470,7 +477,7 @@ void prepare_tc(sra_net *n, const float *params) {
     t.b[L - 1] = n->dev.layer[L - 1].b;
     t.W0 = (const float *)(dev + off_w0);
     t.wout = (const float *)(dev + off_wout);
-    t.bout = params[off + Hn];  // the output layer's bias follows its Hn weights
+    t.bout = params[off + wl];  // the output layer's bias follows its wl weights
     t.L = L;
     t.act = act;
     t.status = (int *)(dev + off_status);

@@ -143,6 +143,8 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
         # widths 64 and 32 on the 128-wide kernel with zero-padded weights
         (wl.make_mlp([64] * 5, "relu", seed=51), dict(arith="truncate", K=16, precision="bf16_sound"), 4, 450, 7),
         (wl.make_mlp([32] * 3, "sin", seed=52), dict(arith="truncate", K=32, precision="bf16"), 5, 200, 7),
+        (wl.make_mlp([96, 200, 64], "relu", seed=53), dict(arith="truncate", K=64, precision="bf16_sound"), 4, 350,
+         7),
     ]
     nets, opts, frontier, segs, out, leaves = setup(sra, specs, seed=9)
     try:
@@ -158,10 +160,10 @@ def test_batch_bf16_segments_equal_lone_rounds(sra):
 
 
 def test_batch_rejects_unserved_bf16(sra):
-    """BF16 segments need the tensor-core path (one hidden width 32, 64, 128,
-    256 or 512; ReLU, ELU or sin) and affine-truncate K = 16, 32, 64 or 128;
-    FP64 and re-checks are not batched."""
-    net = sra.Net(wl.make_mlp([96] * 3, "relu", seed=1))  # width 96: no tensor-core path
+    """BF16 segments need the tensor-core path (3 inputs, hidden widths up to
+    512, all ReLU, all ELU or all sin) and affine-truncate K = 16, 32, 64 or
+    128; FP64 and re-checks are not batched."""
+    net = sra.Net(wl.make_mlp([128] * 3, "relu", seed=1, pe_octaves=1))  # encoded input: no tensor-core path
     net2 = sra.Net(wl.make_mlp([128] * 3, "relu", seed=1))
     try:
         fr = sra.nodes_to_tensor(wl.random_nodes(10, 3))

@@ -54,7 +54,10 @@ NETS = {"relu256x8": wl.net_relu256x8, "relu128x4": lambda: wl.make_mlp([128] * 
         # widths 32 and 64 run the 128-wide kernel on zero-padded weights
         "relu64x4": lambda: wl.make_mlp([64] * 4, "relu", seed=61),
         "elu32x4": lambda: wl.make_mlp([32] * 4, "elu", seed=62),
-        "sin64x3": lambda: wl.make_mlp([64] * 3, "sin", seed=63)}
+        "sin64x3": lambda: wl.make_mlp([64] * 3, "sin", seed=63),
+        # mixed widths run at the width that holds every layer, padded with zeros
+        "relu_mixed": lambda: wl.make_mlp([96, 200, 64, 256], "relu", seed=64),
+        "elu_mixed": lambda: wl.make_mlp([40, 128, 72], "elu", seed=65)}
 
 
 @pytest.mark.parametrize("name", list(NETS))
@@ -231,7 +234,7 @@ def test_bf16_octree_round(sra):
 
 
 def test_bf16_unsupported_shapes(sra):
-    net = sra.Net(wl.make_mlp([96] * 3, "relu", seed=2))  # width 96: no tensor-core path
+    net = sra.Net(wl.make_mlp([128] * 3, "relu", seed=2, pe_octaves=2))  # encoded input: no tensor-core path
     c = torch.zeros((4, 3), device="cuda")
     with pytest.raises(sra.SraError) as e:
         sra.bound_boxes(net, c, c, arith="truncate", K=64, precision="bf16_sound")
@@ -265,7 +268,6 @@ def test_bf16_unsupported_shapes(sra):
 def zero_padded(mlp, H):
     """The same network written out at width H: hidden weights, biases,
     first-layer rows and output weights padded with zeros."""
-    Hn = mlp.widths[1]
     layers = []
     for l in range(mlp.n_layers):
         W, b = mlp.layer(l)
@@ -276,20 +278,23 @@ def zero_padded(mlp, H):
         Wp[:W.shape[0], :W.shape[1]] = W
         bp[:b.shape[0]] = b
         layers.append((Wp, bp))
-    assert Hn < H
+    assert min(mlp.widths[1:-1]) < H
     return wl.make_custom_mlp([3] + [H] * (mlp.n_layers - 1) + [1], mlp.acts, layers)
 
 
-@pytest.mark.parametrize("name,K", [("relu64x4", 64), ("elu32x4", 16), ("sin64x3", 32)])
+@pytest.mark.parametrize("name,K", [("relu64x4", 64), ("elu32x4", 16), ("sin64x3", 32), ("relu_mixed", 64),
+                                    ("elu_mixed", 16)])
 @pytest.mark.parametrize("precision", ["bf16_sound", "bf16"])
 def test_padded_width_equals_explicit_zero_padding(sra, name, K, precision):
-    """A network of width 32 or 64 runs the 128-wide kernel on weights the
-    library pads with zeros: its bounds equal, bit for bit, those of the same
-    network written out at width 128 with zero rows and columns, so the
-    padding adds nothing of its own (sound: the samples test above covers
-    these networks too)."""
+    """A network narrower than the kernel's width somewhere (32 or 64 wide,
+    or of mixed widths) runs on weights the library pads with zeros: its
+    bounds equal, bit for bit, those of the same network written out at the
+    kernel's width with zero rows and columns, so the padding adds nothing
+    of its own (sound: the samples test above covers these networks too)."""
     mlp = NETS[name]()
-    a, b = sra.Net(mlp), sra.Net(zero_padded(mlp, 128))
+    wmax = max(mlp.widths[1:-1])
+    H = 128 if wmax <= 128 else (256 if wmax <= 256 else 512)
+    a, b = sra.Net(mlp), sra.Net(zero_padded(mlp, H))
     c, h = level_boxes(301, seed=17)
     ra = run(sra, a, c, h, arith="truncate", K=K, precision=precision)
     rb = run(sra, b, c, h, arith="truncate", K=K, precision=precision)
@@ -300,15 +305,15 @@ def test_padded_width_equals_explicit_zero_padding(sra, name, K, precision):
 
 
 @pytest.mark.parametrize("name", ["relu256x8", "elu256x3", "sin256x3", "relu512x4", "elu512x3", "relu64x4",
-                                  "elu32x4", "sin64x3"])
+                                  "elu32x4", "sin64x3", "relu_mixed", "elu_mixed"])
 def test_bf16_plain_tracks_oracle(sra, name):
     """Plain BF16 tensor-core bounds (no rounding radius): error against the
     FP64 oracle is stated per box; it comes from the BF16 rounding of the
     noise columns (relative 2^-8 per entry, weights and centers carried as
     BF16 hi/lo pairs). Gates: radius within 2 %, center within 1e-3 of the
     scale, classes equal except where the oracle bound is within that
-    tolerance of zero. On the 32- and 64-wide networks the center gate is
-    2^-7: a neuron's range ends move by up to 2^-8 of its radius, the rules
+    tolerance of zero. On networks with a layer narrower than 128 the center
+    gate is 2^-7: a neuron's range ends move by up to 2^-8 of its radius, the rules
     carry that into its new center, and the short sums of a narrow network
     average out fewer of those roundings (3.6e-3 measured on the 64-wide
     ReLU network; the equality with an explicitly zero-padded network shows
@@ -325,7 +330,7 @@ def test_bf16_plain_tracks_oracle(sra, name):
           f"radius rel err median {np.median(dr):.2e} max {dr.max():.2e}")
     tie = ref["sel_gap"] < 1e-2
     near = np.minimum(np.abs(ref["lo"]), np.abs(ref["hi"])) <= 2e-2 * scale
-    gate_c = 1e-3 if mlp.widths[1] >= 128 else 2.0 ** -7
+    gate_c = 1e-3 if min(mlp.widths[1:-1]) >= 128 else 2.0 ** -7
     assert np.all((dr < 2e-2) | tie)
     assert np.all((dc < gate_c) | tie)
     assert np.all((cls == ref["cls"]) | near | tie)
