@@ -234,10 +234,9 @@ def serving_phase(sra, torch, dev, rates, n_req, slots=4, budget=256 << 20):
              sra.make_opts(arith="fixed", delta=1e-3, max_iters=200, precision="bf16_sound"),  # rays BF16-sound
              sra.make_opts(arith="truncate", K=64, precision="bf16_sound", recheck=True)]  # boxes BF16-sound
 
-    def uniform(m, H):
-        return all(w == H for w in m.widths[1:-1]) and 1 <= m.n_layers - 2 <= 8
-
-    ray_tc = [any(uniform(m, H) for H in (128, 256, 512)) and m.widths[0] <= 64 for m in mlps]
+    # the tensor-core ray kernel: hidden widths up to 512 (narrower layers
+    # padded with zeros), 1 to 8 hidden-to-hidden layers, at most 64 inputs
+    ray_tc = [max(m.widths[1:-1]) <= 512 and 1 <= m.n_layers - 2 <= 8 and m.widths[0] <= 64 for m in mlps]
     box_tc = [tc_box_net(m) for m in mlps]
     o_all, d_all = wl.camera_rays(64, 64)
     ro, rd = torch.from_numpy(o_all).to(dev), torch.from_numpy(d_all).to(dev)

@@ -273,9 +273,11 @@ sra_status sra_classify_and_split_batch(const sra_net *const *nets, const sra_op
  * BF16 storage go to x_inf, the activation rules are the outward-rounded
  * ones (Chebyshev slope only), and the segment's range is rounded outward;
  * the point test f(t + delta) stays a plain evaluation. Both BF16 forms
- * need affine-fixed arithmetic and a network whose hidden layers all have
- * one width H in {128, 256, 512}, with 1 to 8 H -> H layers and an input
- * width (after the encoding) of at most 64; otherwise SRA_EUNSUPPORTED. A
+ * need affine-fixed arithmetic and a network with hidden widths up to 512,
+ * 1 to 8 hidden-to-hidden layers and an input width (after the encoding) of
+ * at most 64 (the kernel runs at the width H in {128, 256, 512} that holds
+ * every hidden layer, narrower layers on weights padded with zeros);
+ * otherwise SRA_EUNSUPPORTED. A
  * bounded wait of that kernel that runs out is reported by sra_sync_status as
  * SRA_ETIMEOUT. With opts->recheck (FP32 or BF16) a ray that took a step
  * whose segment bound [y0 - rad, y0 + rad] has an end within

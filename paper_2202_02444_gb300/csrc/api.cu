@@ -497,21 +497,32 @@ void prepare_tc(sra_net *n, const float *params) {
     n->tc_ok = true;
 }
 
-// Prepare the tensor-core ray kernel if the network has its shape: every
-// hidden width H in {128, 256, 512}, 1 <= L-2 <= 8 hidden H -> H layers, an
-// input width (after the positional encoding) of at most 64, scalar output.
+// Prepare the tensor-core ray kernel if the network has its shape: hidden
+// widths up to 512, 1 <= L-2 <= 8 hidden-to-hidden layers, an input width
+// (after the positional encoding) of at most 64, scalar output. The kernel
+// runs at the width H in {128, 256, 512} that holds every hidden layer;
+// narrower layers are padded with zeros (zero weights, biases and output
+// weights: the padded neurons stay exactly zero, as in the bound kernel).
 // Each layer becomes three BF16 matrices (W_b, W_r, and |W| rounded up);
 // layer 0's K is padded to 64 with zero columns.
 void prepare_tc_rays(sra_net *n, const float *params) {
-    const int L = n->L, H = n->widths.size() > 1 ? n->widths[1] : 0;
-    if (L < 3 || L - 2 > kMaxRayTc || (H != 128 && H != 256 && H != 512)) return;
+    const int L = n->L;
+    if (L < 3 || L - 2 > kMaxRayTc || n->widths.size() != (size_t)L + 1 || n->widths[L] != 1) return;
     if (n->din > tc_ray_max_din()) return;
-    for (int l = 1; l < L; ++l)
-        if (n->widths[l] != H) return;
+    int wmax = 0;
+    for (int l = 1; l < L; ++l) {
+        if (n->widths[l] < 1 || n->widths[l] > 512) return;
+        wmax = std::max(wmax, n->widths[l]);
+    }
+    const int H = wmax <= 128 ? 128 : (wmax <= 256 ? 256 : 512);  // kernel width
     const int nh = L - 2;
     const size_t per_h = (size_t)H * H * 2, per_0 = (size_t)H * 64 * 2;
-    const size_t bytes = 3 * per_0 + 3 * nh * per_h + 256;
+    // W_b, W_r, |W| of layer 0 and the hidden layers; the status word
+    // (256 B); FP32 [H] biases of layers 0 .. L-2 and the output weights [H]
+    const size_t off_status = 3 * per_0 + 3 * nh * per_h, off_bias = off_status + 256;
+    const size_t bytes = off_bias + (size_t)L * H * 4;
     if (cudaMalloc(&n->tcr_buf, bytes) != cudaSuccess) { n->tcr_buf = nullptr; cudaGetLastError(); return; }
+    char *dev = (char *)n->tcr_buf;
     TcRayParams &t = n->tcrp;
     memset(&t, 0, sizeof t);
     // smallest BF16 >= x for x >= 0 (the next bit pattern up is the next
@@ -526,13 +537,13 @@ void prepare_tc_rays(sra_net *n, const float *params) {
         }
         return h;
     };
-    // three matrices of one layer, from W [H][K_in] zero-padded to [H][K]
-    auto upload = [&](const float *W, int k_in, int K, char *dst, TcLayerMaps &maps) -> bool {
+    // three matrices of one layer, from W [out][k_in] zero-padded to [H][K]
+    auto upload = [&](const float *W, int out, int k_in, int K, char *dst, TcLayerMaps &maps) -> bool {
         const size_t per = (size_t)H * K;
         std::vector<__nv_bfloat16> m(3 * per);
         for (int r = 0; r < H; ++r)
             for (int k = 0; k < K; ++k) {
-                const float w = k < k_in ? W[(size_t)r * k_in + k] : 0.f;
+                const float w = (r < out && k < k_in) ? W[(size_t)r * k_in + k] : 0.f;
                 const __nv_bfloat16 h = __float2bfloat16_rn(w);
                 const size_t e = (size_t)r * K + k;
                 m[e] = h;
@@ -545,26 +556,35 @@ void prepare_tc_rays(sra_net *n, const float *params) {
                make_bf16_tile_map(&maps.wr, dst + b, H, K, 128, 64) == 0 &&
                make_bf16_tile_map(&maps.wa, dst + 2 * b, H, K, 128, 64) == 0;
     };
-    bool ok = upload(params, n->din, 64, (char *)n->tcr_buf, t.first);
-    size_t off = (size_t)n->din * H + H;  // layer 1 starts after W0, b0
+    std::vector<float> tail((size_t)L * H, 0.f);  // biases of layers 0 .. L-2, then the output weights
+    const int w1 = n->widths[1];
+    bool ok = upload(params, w1, n->din, 64, dev, t.first);
+    for (int i = 0; i < w1; ++i) tail[i] = params[(size_t)n->din * w1 + i];
+    size_t off = (size_t)n->din * w1 + w1;  // layer 1 starts after W0, b0
     for (int l = 1; ok && l <= nh; ++l) {
-        ok = upload(params + off, H, H, (char *)n->tcr_buf + 3 * per_0 + 3 * (l - 1) * per_h, t.hidden[l - 1]);
-        off += (size_t)H * H + H;
+        const int in = n->widths[l], out = n->widths[l + 1];
+        ok = upload(params + off, out, in, H, dev + 3 * per_0 + 3 * (l - 1) * per_h, t.hidden[l - 1]);
+        for (int i = 0; i < out; ++i) tail[(size_t)l * H + i] = params[off + (size_t)out * in + i];
+        off += (size_t)out * in + out;
     }
+    const int wl = n->widths[L - 1];
+    for (int i = 0; i < wl; ++i) tail[(size_t)(L - 1) * H + i] = params[off + i];
+    ok = ok && cudaMemcpy(dev + off_bias, tail.data(), tail.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) {
         cudaFree(n->tcr_buf);
         n->tcr_buf = nullptr;
         cudaGetLastError();
         return;
     }
-    for (int l = 0; l < L; ++l) t.b[l] = n->dev.layer[l].b;
+    for (int l = 0; l + 1 < L; ++l) t.b[l] = (const float *)(dev + off_bias + (size_t)l * H * 4);
+    t.b[L - 1] = n->dev.layer[L - 1].b;
     for (int l = 0; l + 1 < L; ++l) t.act[l] = n->acts[l];
-    t.wout = n->dev.layer[L - 1].Wt;  // [H][1] == [H]
-    t.bout = params[off + H];
+    t.wout = (const float *)(dev + off_bias + (size_t)(L - 1) * H * 4);
+    t.bout = params[off + wl];  // the output layer's bias follows its wl weights
     t.L = L;
     t.din = n->din;
     t.pe = n->pe;
-    t.status = (int *)((char *)n->tcr_buf + 3 * per_0 + 3 * nh * per_h);
+    t.status = (int *)(dev + off_status);
     // sound form: per linear layer of K inputs, D takes 2 K/16 MMA steps
     // (W_b and W_r) and each |W| x sum of Dx K/16; each 16-deep step adds at
     // most 17 * 2^-23 of its terms' sizes; W_b + W_r is within u_b^2 of W

@@ -101,6 +101,41 @@ def test_tc_rays_plane_analytic(sra, width, precision):
     assert np.median(it) < 100, np.median(it)
 
 
+def zero_padded(mlp, H):
+    """The same network written out with every hidden layer H wide (zero
+    weights, biases and output weights in the padding)."""
+    layers = []
+    for l in range(mlp.n_layers):
+        W, b = mlp.layer(l)
+        o = H if l + 1 < mlp.n_layers else 1
+        i = mlp.widths[0] if l == 0 else H
+        Wp = np.zeros((o, i), np.float32)
+        bp = np.zeros(o, np.float32)
+        Wp[:W.shape[0], :W.shape[1]] = W
+        bp[:b.shape[0]] = b
+        layers.append((Wp, bp))
+    return wl.make_custom_mlp([mlp.widths[0]] + [H] * (mlp.n_layers - 1) + [1], mlp.acts, layers,
+                              pe_octaves=mlp.pe_octaves)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "bf16_sound"])
+@pytest.mark.parametrize("hidden,act,pe,H", [([64] * 3, "relu", 0, 128), ([96, 200, 128], "elu", 2, 256),
+                                             ([40, 40, 40, 40], "sin", 0, 128)])
+def test_tc_rays_padded_widths(sra, hidden, act, pe, H, precision):
+    """Hidden layers narrower than the kernel's width (128, 256 or 512) run on
+    weights padded with zeros: every ray's t and iteration count equal, bit
+    for bit, those of the same network written out at that width, and
+    against the oracle the usual CastRay gate holds."""
+    mlp = wl.make_mlp(hidden, act, seed=70 + len(hidden), pe_octaves=pe)
+    o, d = wl.sphere_rays(203, seed=9, radius=2.0)
+    kw = dict(arith="fixed", precision=precision, delta=1e-3, max_iters=4000 if precision == "bf16" else 12000)
+    t, it = cast(sra, mlp, o, d, **kw)
+    t2, it2 = cast(sra, zero_padded(mlp, H), o, d, **kw)
+    assert np.array_equal(t, t2, equal_nan=True) and np.array_equal(it, it2)
+    ref = oracle.cast_rays(mlp, o, d, "fixed", delta=1e-3, max_iters=kw["max_iters"])
+    check(t, ref, 1e-3, 1e-3, max_frac=0.05)
+
+
 def test_tc_rays_relu256x8(sra):
     """The 3-[256]x8-1 ReLU net: seven hidden layers on the tensor cores."""
     mlp = wl.net_relu256x8()
@@ -148,8 +183,8 @@ def test_tc_rays_iteration_cap(sra):
 def test_tc_rays_unsupported(sra):
     o, d = wl.sphere_rays(8, seed=5, radius=2.0)
     ot, dt = torch.from_numpy(o).cuda(), torch.from_numpy(d).cuda()
-    cases = [(wl.make_mlp([128, 64, 128], "relu", seed=1), "fixed", "bf16", "chebyshev"),  # non-uniform width
-             (wl.make_mlp([96] * 3, "relu", seed=1), "fixed", "bf16", "chebyshev"),       # width not 128/256/512
+    cases = [(wl.make_mlp([128] * 10, "relu", seed=1), "fixed", "bf16", "chebyshev"),     # 9 hidden H -> H layers
+             (wl.make_mlp([128] * 3, "relu", seed=1, pe_octaves=11), "fixed", "bf16", "chebyshev"),  # 69 inputs
              (wl.make_mlp([128] * 3, "relu", seed=1), "truncate", "bf16", "chebyshev"),   # not affine-fixed
              (wl.make_mlp([128] * 3, "relu", seed=1), "fixed", "bf16_sound", "minrange")]  # sound: Chebyshev only
     for mlp, arith, prec, slope in cases:
